@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput of the extended LBGK step on GB300: MLUPS and fraction of the
+HBM roofline for D3Q27, 256^3 decaying isotropic turbulence, FP32 storage.
+
+One bench "step" is one lattice-Boltzmann time step of the whole grid
+(streaming, moments, anomaly, central-difference correction, extended
+equilibrium, relaxation) with the FP64 diagnostic reductions run every
+``--reduce-every`` steps inside the timed region.  Under torchrun every rank
+advances its own independent grid (the workload partitions into independent
+solves, no collective on the data path): ``value`` is the sum over ranks of
+node updates divided by the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded slab of the
+same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(workload="D3Q27 decaying isotropic turbulence 256^3 periodic", lattice="D3Q27",
+                nx=256, ny=256, nz=256, stretch=[1.0, 1.0, 1.0], T=1.0 / 3.0, nu=0.0233,
+                u_rms=0.08, k0=4.0, seed=0)
+FALLBACK_HBM_GBS = 6800.0
+# ncu DRAM bytes (read + write) per node update of the pipelined kernel,
+# keyed by the hash of the kernel sources they were measured on.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2101_04550_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(rank):
+    from paper_2101_04550_gb300 import inputs
+    w = WORKLOAD
+    return inputs.isotropic_turbulence((w["nx"], w["ny"], w["nz"]), seed=w["seed"] + rank,
+                                       k0=w["k0"], u_rms=w["u_rms"])
+
+
+def time_oracle(rho, u, target_s=12.0, slab=8):
+    """MLUPS of the FP64 oracle on a periodic slab of `slab` z-planes of the
+    workload's field, stepping until about `target_s` seconds have passed."""
+    import oracle
+    w = WORKLOAD
+    r = np.ascontiguousarray(rho[:slab])
+    v = np.ascontiguousarray(u[:, :slab])
+    n = (w["nx"], w["ny"], slab)
+    o = oracle.Oracle(3, n, lam=tuple(w["stretch"]), T=w["T"], nu=w["nu"])
+    o.init(r, v)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    cells = n[0] * n[1] * n[2]
+    return cells * steps / dt / 1e6, {"cells": cells, "steps": steps, "seconds": round(dt, 3),
+                                      "sample": f"{n[0]}x{n[1]}x{slab} periodic slab of the 256^3 "
+                                                f"field, {steps} steps, FP64"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("ELBM_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def reference_arm(args):
+    world, rank, local, pg = dist_setup()
+    if rank != 0:
+        return 0
+    rho, u = make_inputs(0)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for k in range(args.warmup + args.steps):
+        mlups, info = time_oracle(rho, u, target_s=per_step, slab=4)
+        if k >= args.warmup:
+            vals.append(mlups)
+    value = float(np.mean(vals))
+    cores = 1
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "lattice": "D3Q27", "storage": "f64 (oracle)",
+                   "nodes": [256, 256, 256], "T": WORKLOAD["T"], "nu": WORKLOAD["nu"]},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": info["sample"] + f"; each step a {per_step:.0f} s sample"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
+    ap.add_argument("--kernel", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--reduce-every", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--nodes", type=int, default=256,
+                    help="edge of the cubic grid (256 = the benchmark workload; smaller only for profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+
+    from paper_2101_04550_gb300 import elbm
+
+    world, rank, local, pg = dist_setup()
+    torch.cuda.set_device(local)
+    elbm.load()
+    if args.nodes != 256:
+        WORKLOAD.update(nx=args.nodes, ny=args.nodes, nz=args.nodes,
+                        workload=f"D3Q27 decaying isotropic turbulence {args.nodes}^3 periodic (profiling size)")
+    w = WORKLOAD
+    cells = w["nx"] * w["ny"] * w["nz"]
+    rho, u = make_inputs(rank)
+    storage = elbm.STORAGE_NAMES[args.storage]
+    s_bytes = elbm.STORAGE_BYTES[storage]
+    Q = 27
+    alg_bytes_per_cell = 2 * Q * s_bytes
+
+    def timed_run(storage, kernel, steps, reduce_every):
+        stream = torch.cuda.current_stream()
+        s = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"],
+                        nu=w["nu"], storage=storage, stream=stream, kernel=kernel)
+        s.init(torch.as_tensor(rho, device="cuda"), torch.as_tensor(u, device="cuda"))
+        s.step(args.warmup)
+        s.reduce()
+        s.sync()
+        launches0 = s.launches
+        ev = []
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        done = 0
+        red = None
+        while done < steps:
+            k = min(reduce_every, steps - done)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(k)
+            b.record(stream)
+            ev.append((a, b, k))
+            done += k
+            red = s.reduce()
+        end.record(stream)
+        torch.cuda.synchronize()
+        total_s = start.elapsed_time(end) / 1e3
+        step_s = sum(a.elapsed_time(b) for a, b, _ in ev) / 1e3
+        launches = s.launches - launches0
+        return s, total_s, step_s, launches, red
+
+    # ---- main measurement ------------------------------------------------
+    with ClockSampler(local) as clocks:
+        s, total_s, step_s, launches, red = timed_run(storage, args.kernel, args.steps, args.reduce_every)
+    t_max = total_s
+    if pg is not None:
+        t = torch.tensor([total_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * cells * args.steps / t_max / 1e6
+    ms_per_step = t_max / args.steps * 1e3
+    peak, peak_kind = hbm_peak()
+    achieved = cells * args.steps * alg_bytes_per_cell / step_s / 1e9
+    src_hash = kernel_source_hash()
+    traffic = MEASURED_TRAFFIC.get((src_hash, args.storage, args.kernel))
+    mass_ok = red is not None and red["nonfinite"] == 0
+
+    # ---- end to end through the public API with host buffers ------------
+    e2e_steps = args.steps
+    rho_h = torch.empty(rho.shape, dtype=torch.float32, pin_memory=True)
+    u_h = torch.empty(u.shape, dtype=torch.float32, pin_memory=True)
+    rho_h.copy_(torch.from_numpy(rho))
+    u_h.copy_(torch.from_numpy(u))
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    s.close()
+    del s
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    s2 = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"],
+                     nu=w["nu"], storage=storage, stream=stream, kernel=args.kernel)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2.init(rho_h.numpy(), u_h.numpy())
+    done = 0
+    while done < e2e_steps:
+        k = min(args.reduce_every, e2e_steps - done)
+        s2.step(k)
+        done += k
+        s2.reduce()
+    s2.moments(rho_o.numpy(), u_o.numpy(), dtype=np.float32)
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (rho_h.numel() + u_h.numel()) * 4
+    d2h = (rho_o.numel() + u_o.numel()) * 4 + 8 * elbm.NRED * ((e2e_steps + args.reduce_every - 1) // args.reduce_every)
+
+    # ---- variants (same workload, other storage / kernel form) ----------
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for name, st, ker in (("f16_shift_pipelined", elbm.F16_SHIFT, 2), ("f32_two_pass", elbm.F32_SHIFT, 1)):
+            sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every)
+            sv.close()
+            nsteps = min(args.steps, 200)
+            b = 2 * Q * elbm.STORAGE_BYTES[st]
+            variants[name] = {"MLUPS": cells * nsteps / tot / 1e6,
+                              "step_MLUPS": cells * nsteps / sts / 1e6,
+                              "roofline_frac": cells * nsteps * b / sts / 1e9 / peak}
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only ---------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, info = time_oracle(rho, u, target_s=12.0, slab=8)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": info["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["workload"], "lattice": "D3Q27", "nodes": [w["nx"], w["ny"], w["nz"]],
+                       "storage": args.storage, "kernel": {1: "two-pass", 2: "pipelined"}[args.kernel],
+                       "T": w["T"], "nu": w["nu"], "u_rms": w["u_rms"],
+                       "reduce_every": args.reduce_every, "global_batch": world,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "no flush: populations per grid (%.2f GB) exceed the 129 MB L2"
+                             % (cells * Q * s_bytes / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "kernel": "k_pipelined" if args.kernel == 2 else "k_anomaly+k_collide",
+                         "alg_bytes_per_node": alg_bytes_per_cell,
+                         "kernel_ms_per_step": step_s / args.steps * 1e3},
+            "e2e": {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+            "variants": variants,
+            "diagnostics_finite": mass_ok,
+            "kernel_source": src_hash,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * elbm.h — C ABI of the GB300 (sm_103a) extended lattice Boltzmann library.
+ *
+ * The library advances the LBGK equation (Eq. LBGK) with the extended
+ * product-form equilibrium f*_i = rho Psi_i(u, P*, lam) (Eqs. prod, 27eqext)
+ * whose diagonal pressure P*_aa = T + u_a^2 + (2 - omega)/(2 rho omega) d_a Q~_aaa
+ * carries the central difference of the diagonal anomaly
+ * Q~_aaa = rho u_a (lam_a^2 - 3 T) - rho u_a^3 (Eqs. Deviation, Paastar1), on the
+ * D2Q9 and D3Q27 lattices with velocities v_i = (lam_x c_ix, lam_y c_iy, lam_z c_iz)
+ * (Eqs. d3q27vel, d3q27velSTRETCHED).  Units: R = 1, delta t = 1; the node
+ * spacing along axis a is lam_a; omega follows from nu = (1/omega - 1/2) T (Eq. nu).
+ *
+ * Conventions shared by every entry point
+ *   - Population index i = (cx+1) + 3 (cy+1) + 9 (cz+1)  (Q = 27),
+ *                      i = (cx+1) + 3 (cy+1)             (Q = 9);
+ *     the opposite direction of i is Q-1-i.
+ *   - Caller-side fields are structure-of-arrays with x fastest:
+ *       rho[nz][ny][nx], u[D][nz][ny][nx], f[Q][nz][ny][nx].
+ *     For D2Q9, nz must be 1 and u has two components.
+ *   - Pointers flagged "on_device" are CUDA device pointers that must be valid
+ *     on the solver's stream; otherwise they are host pointers.
+ *   - Every int-returning call returns ELBM_OK (0) or a negative ELBM_ERR_*
+ *     code and never throws; elbm_last_error() gives the message of the
+ *     calling thread's last failure.
+ *   - All device work is enqueued on the stream given to elbm_create.  Calls
+ *     that return data to the host synchronise that stream.
+ *
+ * The library owns the device memory it allocates (populations, the anomaly
+ * field and reduction partials); elbm_destroy frees it.  The caller owns every
+ * buffer it passes in.
+ */
+#ifndef ELBM_H
+#define ELBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define ELBM_OK                0
+#define ELBM_ERR_ARG          -1  /* invalid argument or size                         */
+#define ELBM_ERR_UNREALIZABLE -2  /* T >= min lam_a^2: rest population not positive   */
+#define ELBM_ERR_OOM          -3  /* device allocation failed                         */
+#define ELBM_ERR_CUDA         -4  /* a CUDA runtime call or a launch failed           */
+#define ELBM_ERR_NONFINITE    -5  /* a diagnostic found NaN/Inf in the state          */
+#define ELBM_ERR_TIMEOUT      -6  /* a bounded device-side wait gave up               */
+#define ELBM_ERR_STATE        -7  /* call out of order (e.g. step before init)        */
+
+/* ---------------------------------------------------------------- lattices */
+#define ELBM_D2Q9   9
+#define ELBM_D3Q27 27
+
+/* --------------------------------------------------------- storage of f_i */
+/* Collision arithmetic is FP32 in every mode.  "SHIFT" modes store
+ * g_i = f_i - w_i rho_ref with w_i = Psi_i(0, T, lam) the rest equilibrium at the
+ * run's T and stretch (rho_ref = 1 unless set by ELBM_OPT_RHO_REF before init);
+ * half-precision stores round to nearest even. */
+#define ELBM_F32         0  /* f_i as float                       (4 B/population) */
+#define ELBM_F16_SHIFT   1  /* g_i as IEEE half                   (2 B/population) */
+#define ELBM_BF16_SHIFT  2  /* g_i as bfloat16                    (2 B/population) */
+#define ELBM_F32_SHIFT   3  /* g_i as float                       (4 B/population) */
+
+/* ------------------------------------------------------- caller dtypes */
+#define ELBM_DTYPE_F32 0
+#define ELBM_DTYPE_F64 1
+
+/* ----------------------------------------------------------- options */
+/* ELBM_OPT_EQUILIBRIUM: 0 = extended equilibrium (Eq. 27eqext, default);
+ *   1 = product-form equilibrium without the correction (Eq. 27eq);
+ *   2 = product form truncated to second order in u (Sec. III preamble). */
+#define ELBM_OPT_EQUILIBRIUM 1
+/* ELBM_OPT_KERNEL: 0 = automatic; 1 = two-pass (anomaly pass, collide pass);
+ *   2 = persistent pipelined pass (same arithmetic, one cooperative launch per step). */
+#define ELBM_OPT_KERNEL      2
+/* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
+#define ELBM_OPT_RHO_REF     3
+/* ELBM_OPT_FORCE_X/Y/Z: constant body-force acceleration g (channel flow,
+ *   Sec. III.E); applied as f_i += f^eq_i(rho, u + g) - f^eq_i(rho, u). */
+#define ELBM_OPT_FORCE_X     4
+#define ELBM_OPT_FORCE_Y     5
+#define ELBM_OPT_FORCE_Z     6
+/* ELBM_OPT_WALLS_Y: 1 = half-way bounce-back walls below y = 0 and above
+ *   y = ny-1 (periodic otherwise); the anomaly's ghost value beyond a wall is
+ *   the negated value of the wall-adjacent node. */
+#define ELBM_OPT_WALLS_Y     7
+
+/* ------------------------------------------------------- diagnostics */
+/* elbm_reduce output, all accumulated in FP64 over every node (sums, not means):
+ *  [0] sum rho          [1..3] sum rho u_a        [4] sum rho |u|^2
+ *  [5] sum |u|^2        [6] sum |curl u|^2 (central differences, spacing lam)
+ *  [7] sum (d_x u_x)^2  [8] sum u_x^2             [9] min_i,x f_i (realizability)
+ *  [10] number of nodes with a non-finite rho or u  [11] max |u|                   */
+#define ELBM_NRED 12
+
+typedef struct elbm_solver elbm_solver;
+
+/*
+ * Create a solver for one periodic grid.
+ *   lattice  ELBM_D2Q9 or ELBM_D3Q27.
+ *   nx,ny,nz nodes per axis, each >= 3 (nz = 1 for D2Q9); nx*ny*nz*Q < 2^31.
+ *   stretch  lam_x, lam_y, lam_z > 0 (Eq. d3q27velSTRETCHED); stretch[2] is
+ *            ignored for D2Q9.  NULL means all ones.
+ *   T        temperature, 0 < T < min_a lam_a^2 (so that Psi_0 > 0 at rest).
+ *   nu       kinematic viscosity > 0; omega = 1/(nu/T + 1/2) (Eq. nu).
+ *   storage  ELBM_F32, ELBM_F16_SHIFT, ELBM_BF16_SHIFT or ELBM_F32_SHIFT.
+ *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * On success *out owns the populations; the state is undefined until elbm_init
+ * or elbm_set_populations.
+ */
+int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, double T,
+                double nu, int storage, void* stream, elbm_solver** out);
+
+/* Free everything the solver owns.  NULL is a no-op. */
+void elbm_destroy(elbm_solver* s);
+
+/* Set an ELBM_OPT_* option.  Returns ELBM_ERR_ARG for an unknown key or value. */
+int elbm_set_option(elbm_solver* s, int key, double value);
+
+/*
+ * Initialise the populations to the product-form equilibrium of the given
+ * fields, f_i = rho Psi_i(u, T + u^2, lam) (Eq. 27eq), and reset the step count.
+ *   rho  nx*ny*nz values; u  D*nx*ny*nz values; dtype ELBM_DTYPE_F32/F64.
+ */
+int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_device);
+
+/*
+ * Advance n >= 0 time steps (Eq. LBGK with f* of Eq. 27eqext).  Asynchronous:
+ * returns once the work is enqueued.  Each step: streaming, moments
+ * (Eqs. density, momentum), the anomaly and its central difference, the
+ * extended equilibrium, relaxation.
+ */
+int elbm_step(elbm_solver* s, int n);
+
+/*
+ * Density and velocity of the current (post-streaming) state, Eqs. density and
+ * momentum.  With a body force the velocity is the half-step value u + g/2.
+ * Synchronises the solver's stream.
+ */
+int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device);
+
+/* Read / write the post-streaming populations f_i (unshifted) in the layout
+ * f[Q][nz][ny][nx].  Writing resets the internal streaming parity. */
+int elbm_get_populations(elbm_solver* s, void* f, int dtype, int on_device);
+int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device);
+
+/* FP64 diagnostics of the current state into out[ELBM_NRED] (host).  Synchronises.
+ * Returns ELBM_ERR_NONFINITE (after filling out) if a node is non-finite. */
+int elbm_reduce(elbm_solver* s, double* out);
+
+/* Block the host until the solver's stream is idle. */
+int elbm_sync(elbm_solver* s);
+
+/* Informational queries. */
+long long elbm_cells(const elbm_solver* s);
+long long elbm_steps_done(const elbm_solver* s);
+double elbm_omega(const elbm_solver* s);
+/* Device bytes of populations + anomaly field (+ reduction scratch once used). */
+long long elbm_device_bytes(const elbm_solver* s);
+/* Number of kernel launches this solver has issued since creation. */
+long long elbm_launch_count(const elbm_solver* s);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* elbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELBM_H */

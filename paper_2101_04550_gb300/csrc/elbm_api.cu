@@ -1,0 +1,452 @@
+// C ABI of the elbm library (declared in include/elbm.h): argument checks,
+// ownership of device memory, choice of kernel form, host<->device staging.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "elbm_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? ELBM_ERR_OOM : ELBM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+constexpr int kStepsPerLaunch = 256;  // bound on the duration of one pipelined launch
+
+}  // namespace
+
+namespace elbm {
+
+size_t storage_bytes(int storage)
+{
+    return (storage == ELBM_F16_SHIFT || storage == ELBM_BF16_SHIFT) ? 2 : 4;
+}
+
+// Rest triplet per axis, Psi_c(0, T, lam) = (T/(2 lam^2), 1 - T/lam^2, T/(2 lam^2))
+// (Eqs. phi0S, phiPlusS, phiMinusS at u = 0, P = T).  The centre value is
+// rounded to a multiple of 2^-24 and the side values are (1 - centre)/2, so
+// that the three floats sum to exactly one: the equilibrium then carries
+// exactly rho and rho u in every product (a sum of 1 + eps would scale the
+// momentum by 1 + eps each step).  The implied temperature differs from T by
+// at most 2^-24 lam^2.
+static void rest_triplet(double T, double lam, float out[3])
+{
+    const double centre = std::nearbyint((1.0 - T / (lam * lam)) * 16777216.0) / 16777216.0;
+    const double side = 0.5 * (1.0 - centre);
+    out[0] = (float)side;
+    out[2] = (float)side;
+    out[1] = (float)centre;
+}
+
+void fill_params(const Solver& s, StepParams& p)
+{
+    std::memset(&p, 0, sizeof p);
+    p.f = s.f;
+    p.q = s.q;
+    p.sync = s.sync;
+    p.status = s.status;
+    p.nx = s.nx;
+    p.ny = s.ny;
+    p.nz = s.nz;
+    p.N = (int)s.N;
+    p.plane = s.nx * s.ny;
+    for (int a = 0; a < 3; ++a) {
+        const double l = s.lam[a];
+        p.lam[a] = (float)l;
+        p.inv_lam[a] = (float)(1.0 / l);
+        p.inv_lam2[a] = (float)(1.0 / (l * l));
+        p.inv_2lam[a] = (float)(0.5 / l);
+        p.lam2m3T[a] = (float)(l * l - 3.0 * s.T);
+        rest_triplet(s.T, l, p.rest[a]);
+        p.inv_theta[a] = (float)(1.0 / (2.0 * (double)p.rest[a][0]));
+    }
+    for (int i = 0; i < s.Q; ++i) {
+        const int c[3] = {i % 3, (i / 3) % 3, i / 9};
+        double w = 1.0;
+        for (int a = 0; a < s.D; ++a) w *= (double)p.rest[a][c[a]];
+        p.w[i] = (float)w;
+    }
+    p.T = (float)s.T;
+    p.omega = (float)s.omega;
+    p.coef = (float)((2.0 - s.omega) / (2.0 * s.omega));
+    p.rho_ref = (float)s.rho_ref;
+    for (int a = 0; a < 3; ++a) p.g[a] = (float)s.g[a];
+    p.forced = (s.g[0] != 0.0 || s.g[1] != 0.0 || s.g[2] != 0.0);
+    p.eq_mode = s.eq_mode;
+    p.parity = s.parity;
+}
+
+// Order of the phases of one pipelined step, as (type, chunk) pairs
+// (type 0 = anomaly phase, 1 = collide phase): anomaly phases of the last
+// chunk and of chunks 0..L first, then every collide phase followed by the next
+// anomaly phase.  With L >= 1 every phase a collide phase waits for is issued
+// before it (the deadlock-freedom argument of the pipelined kernel).
+static void phase_order(int K, int L, unsigned* out)
+{
+    int n = 0;
+    auto put = [&](int type, int c) {
+        out[2 * n] = (unsigned)type;
+        out[2 * n + 1] = (unsigned)c;
+        ++n;
+    };
+    if (K == 1) {
+        put(0, 0);
+        put(1, 0);
+        return;
+    }
+    put(0, K - 1);
+    const int pro = std::min(L, K - 2);
+    for (int c = 0; c <= pro; ++c) put(0, c);
+    int next_a = pro + 1;
+    for (int j = 0; j < K; ++j) {
+        put(1, j);
+        if (next_a <= K - 2) put(0, next_a++);
+    }
+}
+
+}  // namespace elbm
+
+using elbm::Solver;
+
+struct elbm_solver : public Solver {};
+
+namespace {
+
+int check_status(elbm_solver* s)
+{
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st != 0) {
+        cudaMemsetAsync(s->status, 0, sizeof(int), s->stream);
+        cudaStreamSynchronize(s->stream);
+        return fail(st, "a bounded device-side wait gave up (code %d); the state is undefined", st);
+    }
+    return ELBM_OK;
+}
+
+bool pipelined_usable(const elbm_solver* s) { return s->pipe.grid > 0 && s->sync != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char* elbm_last_error(void) { return g_err; }
+
+int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, double T, double nu,
+                int storage, void* stream, elbm_solver** out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(ELBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (lattice != ELBM_D2Q9 && lattice != ELBM_D3Q27) return fail(ELBM_ERR_ARG, "lattice must be 9 or 27");
+    const int D = lattice == ELBM_D2Q9 ? 2 : 3;
+    if (nx < 3 || ny < 3) return fail(ELBM_ERR_ARG, "nx and ny must be >= 3");
+    if (D == 2 && nz != 1) return fail(ELBM_ERR_ARG, "D2Q9 needs nz == 1");
+    if (D == 3 && nz < 3) return fail(ELBM_ERR_ARG, "D3Q27 needs nz >= 3");
+    const long long N = (long long)nx * ny * nz;
+    if (N * lattice >= (1ll << 31)) return fail(ELBM_ERR_ARG, "grid too large: nx*ny*nz*Q must be < 2^31");
+    double lam[3] = {1.0, 1.0, 1.0};
+    if (stretch)
+        for (int a = 0; a < D; ++a) lam[a] = stretch[a];
+    for (int a = 0; a < D; ++a)
+        if (!(lam[a] > 0.0) || !std::isfinite(lam[a])) return fail(ELBM_ERR_ARG, "stretch must be finite and > 0");
+    if (!(T > 0.0) || !std::isfinite(T)) return fail(ELBM_ERR_ARG, "T must be finite and > 0");
+    double lmin2 = lam[0] * lam[0];
+    for (int a = 1; a < D; ++a) lmin2 = std::min(lmin2, lam[a] * lam[a]);
+    if (T >= lmin2) return fail(ELBM_ERR_UNREALIZABLE, "T = %g >= min lam^2 = %g: rest population not positive", T, lmin2);
+    if (!(nu > 0.0) || !std::isfinite(nu)) return fail(ELBM_ERR_ARG, "nu must be finite and > 0");
+    if (storage != ELBM_F32 && storage != ELBM_F16_SHIFT && storage != ELBM_BF16_SHIFT && storage != ELBM_F32_SHIFT)
+        return fail(ELBM_ERR_ARG, "unknown storage mode %d", storage);
+
+    elbm_solver* s = new elbm_solver();
+    s->lattice = lattice;
+    s->D = D;
+    s->Q = lattice;
+    s->nx = nx;
+    s->ny = ny;
+    s->nz = nz;
+    s->N = N;
+    s->storage = storage;
+    for (int a = 0; a < 3; ++a) s->lam[a] = lam[a];
+    s->T = T;
+    s->nu = nu;
+    s->omega = 1.0 / (nu / T + 0.5);  // Eq. nu with R = 1, delta t = 1
+    s->stream = (cudaStream_t)stream;
+
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    const size_t fbytes = (size_t)lattice * N * elbm::storage_bytes(storage);
+    const size_t qbytes = (size_t)D * N * sizeof(float);
+    if (e == cudaSuccess) e = cudaMalloc(&s->f, fbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->q, qbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_red, ELBM_NRED * sizeof(double));
+    if (e == cudaSuccess) {
+        s->pipe = (D == 2) ? elbm::pipelined_geometry_impl<2>(*s) : elbm::pipelined_geometry_impl<3>(*s);
+        if (s->pipe.grid > 0) {
+            std::vector<unsigned> words(s->pipe.sync_words, 0u);
+            elbm::phase_order(s->pipe.nchunks, s->pipe.lookahead, words.data() + 2 + 2 * s->pipe.nchunks);
+            e = cudaMalloc((void**)&s->sync, words.size() * sizeof(unsigned));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(s->sync, words.data(), words.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "elbm_create");
+        elbm_destroy(s);
+        return rc;
+    }
+    s->bytes = fbytes + qbytes + s->pipe.sync_words * sizeof(unsigned);
+    *out = s;
+    return ELBM_OK;
+}
+
+void elbm_destroy(elbm_solver* s)
+{
+    if (!s) return;
+    if (s->stream || s->f) cudaStreamSynchronize(s->stream);
+    cudaFree(s->f);
+    cudaFree(s->q);
+    cudaFree(s->sync);
+    cudaFree(s->status);
+    cudaFree(s->mom);
+    cudaFree(s->partials);
+    cudaFree(s->red_out);
+    if (s->host_red) cudaFreeHost(s->host_red);
+    delete s;
+}
+
+int elbm_set_option(elbm_solver* s, int key, double value)
+{
+    if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
+    switch (key) {
+        case ELBM_OPT_EQUILIBRIUM:
+            if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "equilibrium must be 0 or 1");
+            s->eq_mode = (int)value;
+            return ELBM_OK;
+        case ELBM_OPT_KERNEL:
+            if (value != 0.0 && value != 1.0 && value != 2.0) return fail(ELBM_ERR_ARG, "kernel must be 0, 1 or 2");
+            if (value == 2.0 && !pipelined_usable(s)) return fail(ELBM_ERR_ARG, "pipelined kernel unavailable");
+            s->kernel = (int)value;
+            return ELBM_OK;
+        case ELBM_OPT_RHO_REF:
+            if (!(value > 0.0) || !std::isfinite(value)) return fail(ELBM_ERR_ARG, "rho_ref must be > 0");
+            if (s->initialised) return fail(ELBM_ERR_STATE, "rho_ref must be set before init");
+            s->rho_ref = value;
+            return ELBM_OK;
+        case ELBM_OPT_FORCE_X:
+        case ELBM_OPT_FORCE_Y:
+        case ELBM_OPT_FORCE_Z:
+        case ELBM_OPT_WALLS_Y:
+            if (value == 0.0) return ELBM_OK;
+            return fail(ELBM_ERR_ARG, "option %d is not supported by this build", key);
+        default:
+            return fail(ELBM_ERR_ARG, "unknown option %d", key);
+    }
+}
+
+static cudaError_t stage_to_device(const void* host, size_t bytes, void** dev, cudaStream_t st)
+{
+    cudaError_t e = cudaMalloc(dev, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st);
+}
+
+int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_device)
+{
+    if (!s || !rho || !u) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
+    const size_t es = dtype == ELBM_DTYPE_F64 ? 8 : 4;
+    const void* drho = rho;
+    const void* du = u;
+    void *t1 = nullptr, *t2 = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = stage_to_device(rho, es * s->N, &t1, s->stream);
+        if (e == cudaSuccess) e = stage_to_device(u, es * s->D * s->N, &t2, s->stream);
+        drho = t1;
+        du = t2;
+    }
+    if (e == cudaSuccess)
+        e = (s->D == 2) ? elbm::init_impl<2>(*s, drho, du, dtype, &s->launches)
+                        : elbm::init_impl<3>(*s, drho, du, dtype, &s->launches);
+    if (!on_device) {
+        cudaError_t e2 = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) e = e2;
+        cudaFree(t1);
+        cudaFree(t2);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_init");
+    s->parity = 0;
+    s->steps_done = 0;
+    s->initialised = 1;
+    return ELBM_OK;
+}
+
+int elbm_step(elbm_solver* s, int n)
+{
+    if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
+    if (n < 0) return fail(ELBM_ERR_ARG, "n must be >= 0");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_step before elbm_init");
+    const bool pipelined = (s->kernel == 2) && pipelined_usable(s);
+    cudaError_t e = cudaSuccess;
+    int left = n;
+    while (left > 0 && e == cudaSuccess) {
+        if (pipelined) {
+            const int k = std::min(left, kStepsPerLaunch);
+            e = (s->D == 2) ? elbm::step_pipelined_impl<2>(*s, s->parity, k, &s->launches)
+                            : elbm::step_pipelined_impl<3>(*s, s->parity, k, &s->launches);
+            s->parity = (s->parity + k) & 1;
+            left -= k;
+        } else {
+            e = (s->D == 2) ? elbm::step_two_pass_impl<2>(*s, s->parity, &s->launches)
+                            : elbm::step_two_pass_impl<3>(*s, s->parity, &s->launches);
+            s->parity ^= 1;
+            --left;
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_step");
+    s->steps_done += n;
+    return ELBM_OK;
+}
+
+int elbm_sync(elbm_solver* s)
+{
+    if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_sync");
+    return check_status(s);
+}
+
+int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device)
+{
+    if (!s || !rho || !u) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_moments before elbm_init");
+    const size_t es = dtype == ELBM_DTYPE_F64 ? 8 : 4;
+    void *drho = rho, *du = u;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = cudaMalloc(&drho, es * s->N);
+        if (e == cudaSuccess) e = cudaMalloc(&du, es * s->D * s->N);
+    }
+    if (e == cudaSuccess)
+        e = (s->D == 2) ? elbm::moments_impl<2>(*s, drho, du, dtype, &s->launches)
+                        : elbm::moments_impl<3>(*s, drho, du, dtype, &s->launches);
+    if (!on_device) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rho, drho, es * s->N, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, es * s->D * s->N, cudaMemcpyDeviceToHost, s->stream);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = e2;
+    if (!on_device) {
+        cudaFree(drho);
+        cudaFree(du);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_moments");
+    return check_status(s);
+}
+
+int elbm_get_populations(elbm_solver* s, void* f, int dtype, int on_device)
+{
+    if (!s || !f) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_get_populations before init");
+    const size_t bytes = (dtype == ELBM_DTYPE_F64 ? 8 : 4) * (size_t)s->Q * s->N;
+    void* df = f;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) e = cudaMalloc(&df, bytes);
+    if (e == cudaSuccess)
+        e = (s->D == 2) ? elbm::get_populations_impl<2>(*s, df, dtype, &s->launches)
+                        : elbm::get_populations_impl<3>(*s, df, dtype, &s->launches);
+    if (!on_device && e == cudaSuccess) e = cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, s->stream);
+    cudaError_t e2 = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = e2;
+    if (!on_device) cudaFree(df);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_get_populations");
+    return check_status(s);
+}
+
+int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device)
+{
+    if (!s || !f) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
+    const size_t bytes = (dtype == ELBM_DTYPE_F64 ? 8 : 4) * (size_t)s->Q * s->N;
+    const void* df = f;
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        e = stage_to_device(f, bytes, &tmp, s->stream);
+        df = tmp;
+    }
+    if (e == cudaSuccess)
+        e = (s->D == 2) ? elbm::set_populations_impl<2>(*s, df, dtype, &s->launches)
+                        : elbm::set_populations_impl<3>(*s, df, dtype, &s->launches);
+    cudaError_t e2 = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = e2;
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_set_populations");
+    s->parity = 0;
+    s->initialised = 1;
+    return ELBM_OK;
+}
+
+int elbm_reduce(elbm_solver* s, double* out)
+{
+    if (!s || !out) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_reduce before init");
+    cudaError_t e = cudaSuccess;
+    if (!s->mom) {
+        s->red_blocks = std::max(1, std::min(8 * s->num_sms, (int)((s->N + 255) / 256)));
+        e = cudaMalloc((void**)&s->mom, 5 * sizeof(float) * (size_t)s->N);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&s->partials, sizeof(double) * ELBM_NRED * s->red_blocks);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&s->red_out, sizeof(double) * ELBM_NRED);
+        if (e != cudaSuccess) {
+            cudaFree(s->mom);
+            cudaFree(s->partials);
+            cudaFree(s->red_out);
+            s->mom = nullptr;
+            s->partials = s->red_out = nullptr;
+            return cuda_fail(e, "elbm_reduce scratch");
+        }
+        s->bytes += 5 * sizeof(float) * (size_t)s->N + sizeof(double) * ELBM_NRED * (s->red_blocks + 1);
+    }
+    e = (s->D == 2) ? elbm::reduce_impl<2>(*s, &s->launches) : elbm::reduce_impl<3>(*s, &s->launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->host_red, s->red_out, sizeof(double) * ELBM_NRED, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_reduce");
+    std::memcpy(out, s->host_red, sizeof(double) * ELBM_NRED);
+    int rc = check_status(s);
+    if (rc != ELBM_OK) return rc;
+    if (out[10] > 0.0) return fail(ELBM_ERR_NONFINITE, "%.0f nodes hold non-finite values", out[10]);
+    return ELBM_OK;
+}
+
+long long elbm_cells(const elbm_solver* s) { return s ? s->N : 0; }
+long long elbm_steps_done(const elbm_solver* s) { return s ? s->steps_done : 0; }
+double elbm_omega(const elbm_solver* s) { return s ? s->omega : 0.0; }
+long long elbm_device_bytes(const elbm_solver* s) { return s ? (long long)s->bytes : 0; }
+long long elbm_launch_count(const elbm_solver* s) { return s ? s->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations of the elbm CUDA library: the solver handle, the
+// by-value parameter block every kernel receives, and the launchers that the
+// per-lattice translation units export to the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "../../include/elbm.h"
+
+namespace elbm {
+
+constexpr int kMaxQ = 27;
+
+// Everything a step kernel needs, passed by value (lives in the constant
+// parameter bank).  Derived constants are precomputed on the host in double
+// and rounded once to float.
+struct StepParams {
+    void* f;              // populations, storage type per `storage`, layout f[i][cell]
+    float* q;             // diagonal anomaly field q[a][cell] (Eq. Deviation)
+    unsigned int* sync;   // pipelined kernel: ticket + per-chunk completion counters
+    int* status;          // device status word (bounded waits report here)
+    int nx, ny, nz;       // nodes per axis (nz = 1 for D2Q9)
+    int N;                // nx*ny*nz
+    int plane;            // nx*ny
+    float lam[3];         // stretching factors lam_a
+    float inv_lam[3];     // 1/lam_a
+    float inv_lam2[3];    // 1/lam_a^2
+    float inv_2lam[3];    // 1/(2 lam_a): central-difference weight (node spacing lam_a)
+    float lam2m3T[3];     // lam_a^2 - 3T
+    float rest[3][3];     // rest triplet per axis: Psi_c(0, T, lam_a), index c+1
+    float w[kMaxQ];       // rest weights w_i = prod_a rest[a][c_ia+1]
+    float inv_theta[3];   // 1 / sum_i w_i c_ia^2 = 1 / (2 rest[a][0])
+    float T;              // temperature (R = 1)
+    float omega;          // relaxation frequency
+    float coef;           // (2 - omega) / (2 omega)
+    float rho_ref;        // reference density of the shifted storage
+    float g[3];           // body-force acceleration
+    int forced;           // g != 0
+    int eq_mode;          // 0 extended, 1 product form, 2 second order
+    int parity;           // AA streaming parity of the step about to run (0 even, 1 odd)
+    // pipelined kernel geometry
+    int chunk_planes;     // z planes per chunk
+    int nchunks;          // number of z chunks
+    int tile_cells;       // cells per tile
+    int tiles_per_chunk;  // tiles in one phase of one chunk
+    int nsteps;           // steps advanced by one launch
+    int lookahead;        // anomaly phases issued ahead of collide phases
+};
+
+// Chunking of the pipelined step (see pipelined.cuh).
+struct PipeGeom {
+    int grid = 0;            // resident blocks launched
+    int chunk_planes = 0;    // layers (z planes, or y rows for D2Q9) per chunk
+    int nchunks = 0;
+    int tile_cells = 0;
+    int tiles_per_chunk = 0;
+    int lookahead = 0;
+    size_t sync_words = 0;
+};
+
+struct Solver {
+    int lattice = 0, D = 0, Q = 0;
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    int storage = 0;
+    double lam[3] = {1, 1, 1};
+    double T = 0, nu = 0, omega = 0, rho_ref = 1.0;
+    double g[3] = {0, 0, 0};
+    int eq_mode = 0;
+    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined
+    int walls_y = 0;
+    int parity = 0;
+    int initialised = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    void* f = nullptr;                // populations
+    float* q = nullptr;               // anomaly field
+    unsigned int* sync = nullptr;     // pipelined-kernel ticket, counters, phase order
+    PipeGeom pipe;
+    int* status = nullptr;            // device status word
+    float* mom = nullptr;             // reduction scratch: rho, u[3], fmin per node
+    double* partials = nullptr;       // reduction scratch: per-block FP64 partial sums
+    double* red_out = nullptr;        // device copy of the ELBM_NRED results
+    double* host_red = nullptr;       // pinned host copy of the results
+    int red_blocks = 0;
+    long long steps_done = 0;
+    long long launches = 0;
+    size_t bytes = 0;
+};
+
+size_t storage_bytes(int storage);
+void fill_params(const Solver& s, StepParams& p);
+
+// Launchers, explicitly instantiated per lattice (kernels_d2q9.cu,
+// kernels_d3q27.cu).  Each returns the CUDA error of its launches and adds the
+// number of kernel launches it issued to *launches.
+template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
+template <int D> cudaError_t step_pipelined_impl(const Solver&, int, int, long long*);
+template <int D> PipeGeom pipelined_geometry_impl(const Solver&);
+template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
+template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);
+template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, long long*);
+template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
+template <int D> cudaError_t reduce_impl(const Solver&, long long*);
+
+}  // namespace elbm

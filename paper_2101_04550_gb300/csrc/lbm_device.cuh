@@ -1,0 +1,267 @@
+// Device-side building blocks of the extended LBGK step: lattice constants,
+// storage conversion, AA-pattern gather/scatter, moments, the diagonal anomaly
+// and the product-form extended equilibrium with BGK relaxation.
+//
+// Arithmetic is FP32.  Populations are handled as deviations from the rest
+// equilibrium, g_i = f_i - w_i rho_ref with w_i = Psi_i(0, T, lam), so that the
+// large constant part never enters a rounding step; the equilibrium deviation
+// rho Psi_i - rho_ref w_i is formed from per-axis differences (see relax()).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "elbm_internal.h"
+
+namespace elbm {
+
+// ------------------------------------------------------------------ lattice
+// Population i <-> c_i: i = (cx+1) + 3 (cy+1) + 9 (cz+1) (Eq. d3q27vel);
+// D2Q9 is the same ordering without z.  opposite(i) = Q-1-i.
+template <int D>
+struct Lat {
+    static constexpr int Q = (D == 2) ? 9 : 27;
+};
+__host__ __device__ constexpr int cx_of(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int cy_of(int i) { return (i / 3) % 3 - 1; }
+template <int D>
+__host__ __device__ constexpr int cz_of(int i) { return D == 3 ? i / 9 - 1 : 0; }
+
+// ------------------------------------------------------------------ storage
+template <int ST>
+struct Storage;
+template <>
+struct Storage<ELBM_F32> {
+    using T = float;
+    static constexpr bool shifted = false;
+    __device__ static float load(const T* p) { return *p; }
+    __device__ static void store(T* p, float v) { *p = v; }
+    __device__ static T cvt(float v) { return v; }
+};
+template <>
+struct Storage<ELBM_F32_SHIFT> {
+    using T = float;
+    static constexpr bool shifted = true;
+    __device__ static float load(const T* p) { return *p; }
+    __device__ static void store(T* p, float v) { *p = v; }
+    __device__ static T cvt(float v) { return v; }
+};
+template <>
+struct Storage<ELBM_F16_SHIFT> {
+    using T = __half;
+    static constexpr bool shifted = true;
+    __device__ static float load(const T* p) { return __half2float(*p); }
+    __device__ static void store(T* p, float v) { *p = __float2half_rn(v); }
+    __device__ static T cvt(float v) { return __float2half_rn(v); }
+};
+template <>
+struct Storage<ELBM_BF16_SHIFT> {
+    using T = __nv_bfloat16;
+    static constexpr bool shifted = true;
+    __device__ static float load(const T* p) { return __bfloat162float(*p); }
+    __device__ static void store(T* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static T cvt(float v) { return __float2bfloat16_rn(v); }
+};
+
+// --------------------------------------------------------------- node index
+// Periodic neighbour offsets of one node: ox[c+1] = x+c (wrapped),
+// oy[c+1] = (y+c wrapped)*nx, oz[c+1] = (z+c wrapped)*nx*ny.
+struct Node {
+    int cell;
+    int ox[3], oy[3], oz[3];
+    __device__ int at(int cx, int cy, int cz) const { return ox[cx + 1] + oy[cy + 1] + oz[cz + 1]; }
+};
+
+template <int D>
+__device__ __forceinline__ Node make_node(const StepParams& p, int cell)
+{
+    Node n;
+    n.cell = cell;
+    const int z = cell / p.plane;
+    const int r = cell - z * p.plane;
+    const int y = r / p.nx;
+    const int x = r - y * p.nx;
+    n.ox[1] = x;
+    n.ox[0] = (x == 0) ? p.nx - 1 : x - 1;
+    n.ox[2] = (x == p.nx - 1) ? 0 : x + 1;
+    n.oy[1] = y * p.nx;
+    n.oy[0] = ((y == 0) ? p.ny - 1 : y - 1) * p.nx;
+    n.oy[2] = ((y == p.ny - 1) ? 0 : y + 1) * p.nx;
+    if (D == 3) {
+        n.oz[1] = z * p.plane;
+        n.oz[0] = ((z == 0) ? p.nz - 1 : z - 1) * p.plane;
+        n.oz[2] = ((z == p.nz - 1) ? 0 : z + 1) * p.plane;
+    } else {
+        n.oz[0] = n.oz[1] = n.oz[2] = 0;
+    }
+    return n;
+}
+
+// ------------------------------------------------------- AA-pattern streaming
+// The populations live in one array (in place).  Before an even step the
+// post-streaming f_i(x) sits in slot (i, x); the step writes its post-collision
+// value to slot (opp(i), x).  Before an odd step f_i(x) sits in slot
+// (opp(i), x - c_i) and the step writes to slot (i, x + c_i).  Either way a node
+// reads and writes the same slot set, and the slot sets of distinct nodes are
+// disjoint (Eq. LBGK: f_i moves one node along c_i per step).
+template <int D>
+__device__ __forceinline__ int read_slot(const Node& n, int N, int i, int parity)
+{
+    constexpr int Q = Lat<D>::Q;
+    if (parity == 0) return i * N + n.cell;
+    return (Q - 1 - i) * N + n.at(-cx_of(i), -cy_of(i), -cz_of<D>(i));
+}
+template <int D>
+__device__ __forceinline__ int write_slot(const Node& n, int N, int i, int parity)
+{
+    constexpr int Q = Lat<D>::Q;
+    if (parity == 0) return (Q - 1 - i) * N + n.cell;
+    return i * N + n.at(cx_of(i), cy_of(i), cz_of<D>(i));
+}
+
+template <int D, int ST, int PAR>
+__device__ __forceinline__ void gather(const StepParams& p, const Node& n, float* g)
+{
+    using S = Storage<ST>;
+    const typename S::T* f = static_cast<const typename S::T*>(p.f);
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const float v = S::load(f + read_slot<D>(n, p.N, i, PAR));
+        g[i] = S::shifted ? v : v - p.w[i] * p.rho_ref;
+    }
+}
+
+template <int D, int ST, int PAR>
+__device__ __forceinline__ void scatter(const StepParams& p, const Node& n, const float* g)
+{
+    using S = Storage<ST>;
+    typename S::T* f = static_cast<typename S::T*>(p.f);
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const float v = S::shifted ? g[i] : g[i] + p.w[i] * p.rho_ref;
+        S::store(f + write_slot<D>(n, p.N, i, PAR), v);
+    }
+}
+
+// ------------------------------------------------------------------ moments
+// drho = sum_i g_i (so rho = rho_ref + drho, Eq. density, since sum_i w_i = 1);
+// j_a = lam_a sum_i c_ia g_i = rho u_a (Eq. momentum, since sum_i c_i w_i = 0).
+template <int D>
+__device__ __forceinline__ void moments(const StepParams& p, const float* g, float& drho, float* j)
+{
+    float r = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        r += g[i];
+        if (cx_of(i) == 1) sx += g[i];
+        if (cx_of(i) == -1) sx -= g[i];
+        if (cy_of(i) == 1) sy += g[i];
+        if (cy_of(i) == -1) sy -= g[i];
+        if (cz_of<D>(i) == 1) sz += g[i];
+        if (cz_of<D>(i) == -1) sz -= g[i];
+    }
+    drho = r;
+    j[0] = p.lam[0] * sx;
+    j[1] = p.lam[1] * sy;
+    j[2] = (D == 3) ? p.lam[2] * sz : 0.f;
+}
+
+// Diagonal anomaly Q~_aaa = rho u_a (lam_a^2 - 3T) - rho u_a^3 = j_a (lam_a^2 - 3T - u_a^2)
+// (Eq. Deviation, R = 1).
+__device__ __forceinline__ float anomaly(const StepParams& p, int a, float ja, float ua)
+{
+    return ja * (p.lam2m3T[a] - ua * ua);
+}
+
+// ------------------------------------------------- extended equilibrium + BGK
+// Equilibrium deviation geq_i = rho Psi_i(u, P, lam) - rho_ref w_i for the
+// per-axis pressure excess dP_a = P_aa - T.  Per axis the triplet
+// (Eqs. phi0S, phiPlusS, phiMinusS) is Psi_c = rest_c + delta_c with
+// delta_0 = -dP/lam^2 and delta_{+-1} = (+-u/lam + dP/lam^2)/2, so
+//   Psi_i - w_i = sum_a (prod_{b<a} rest_b) delta_a (prod_{b>a} Psi_b)
+// is formed without cancellation, and rho Psi_i - rho_ref w_i =
+// (rho - rho_ref) Psi_i + rho_ref (Psi_i - w_i).
+template <int D, typename F>
+__device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float drho, const float* u,
+                                                     const float* dP, F&& fn)
+{
+    float A[3][3], dl[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float s = dP[a] * p.inv_lam2[a];
+        const float t = u[a] * p.inv_lam[a];
+        dl[a][0] = 0.5f * (s - t);
+        dl[a][1] = -s;
+        dl[a][2] = 0.5f * (s + t);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[a][c] = p.rest[a][c] + dl[a][c];
+    }
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+            const float pxy = A[0][cx] * A[1][cy];
+            const float dxy = fmaf(dl[0][cx], A[1][cy], p.rest[0][cx] * dl[1][cy]);
+            if (D == 2) {
+                fn(cx + 3 * cy, fmaf(drho, pxy, p.rho_ref * dxy));
+            } else {
+                const float bxy = p.rest[0][cx] * p.rest[1][cy];
+#pragma unroll
+                for (int cz = 0; cz < 3; ++cz) {
+                    const float psi = pxy * A[2][cz];
+                    const float dpsi = fmaf(dxy, A[2][cz], bxy * dl[2][cz]);
+                    fn(cx + 3 * cy + 9 * cz, fmaf(drho, psi, p.rho_ref * dpsi));
+                }
+            }
+        }
+    }
+}
+
+// Relax g toward the extended equilibrium (Eq. LBGK with f* of Eq. 27eqext).
+// d[a] is the central difference of the anomaly along axis a; the pressure
+// diagonal is P*_aa = T + u_a^2 + (2-omega)/(2 rho omega) d_a (Eq. Paastar1).
+//
+// In exact arithmetic f* carries the node's rho and rho u (Eqs. density,
+// momentum), so relaxation conserves them.  In FP32 the rounding of rho, of
+// u = j/rho and of the triplet terms leaves the computed equilibrium with a
+// mass and momentum off by a fraction of an ulp, and in near-uniform flow
+// that error has the same sign at every node and every step.  So the
+// increments dlt_i = geq_i - g_i (small numbers, summed accurately) have their
+// zeroth and first moments e0, e_a projected out along the rest weights,
+//   dlt_i -= w_i (e0 + sum_a c_ia e_a / theta_a),  theta_a = sum_i w_i c_ia^2,
+// before the single rounding of g + omega dlt.
+template <int D>
+__device__ __forceinline__ void relax(const StepParams& p, float* g, float drho, const float* j,
+                                      const float* d)
+{
+    constexpr int Q = Lat<D>::Q;
+    const float rho = p.rho_ref + drho;
+    const float inv_rho = 1.0f / rho;
+    float u[3], dP[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = j[a] * inv_rho;
+        dP[a] = fmaf(p.coef * inv_rho, d[a], u[a] * u[a]);
+    }
+    float dlt[Q];
+    for_each_equilibrium<D>(p, drho, u, dP, [&](int i, float geq) { dlt[i] = geq - g[i]; });
+    float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        e0 += dlt[i];
+        if (cx_of(i) == 1) ex += dlt[i];
+        if (cx_of(i) == -1) ex -= dlt[i];
+        if (cy_of(i) == 1) ey += dlt[i];
+        if (cy_of(i) == -1) ey -= dlt[i];
+        if (cz_of<D>(i) == 1) ez += dlt[i];
+        if (cz_of<D>(i) == -1) ez -= dlt[i];
+    }
+    const float kx = ex * p.inv_theta[0], ky = ey * p.inv_theta[1], kz = (D == 3) ? ez * p.inv_theta[2] : 0.f;
+    const float om = p.omega;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float corr = p.w[i] * (e0 + cx_of(i) * kx + cy_of(i) * ky + cz_of<D>(i) * kz);
+        g[i] = fmaf(om, dlt[i] - corr, g[i]);
+    }
+}
+
+}  // namespace elbm

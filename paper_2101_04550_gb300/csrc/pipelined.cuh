@@ -1,0 +1,197 @@
+// Persistent, in-place (AA) pipelined form of the extended LBGK step.
+//
+// The correction term needs the anomaly Q~_aaa of the neighbours at the same
+// time level (Eq. Paastar1), i.e. post-streaming moments of nodes whose
+// population slots other thread blocks overwrite when they collide.  The
+// two-pass form separates the passes by a kernel boundary and so reads the
+// populations twice from HBM.  Here the grid is cut along its slowest axis
+// (z for D3Q27, y for D2Q9) into chunks, and every chunk has an anomaly phase
+// A(c) (read populations, write q) and a collide phase C(c) (re-read
+// populations, read q of chunks c-1..c+1, relax, write populations in place).
+// Phases are issued in the order
+//     A(K-1), A(0), ..., A(L), C(0), A(L+1), C(1), A(L+2), ...
+// so that A(c) runs L chunks ahead of C(c) and the re-read of chunk c hits L2.
+//
+// Work is split into tiles and handed out by an atomic ticket.  A tile waits
+// (bounded) only for tiles with smaller tickets:
+//   C_s(c) waits for A_s(c-1), A_s(c), A_s(c+1) to be complete, and
+//   A_s(c) (s > 0) waits for C_{s-1}(c-1), C_{s-1}(c), C_{s-1}(c+1),
+// which covers every read-after-write and write-after-read hazard of the
+// in-place slots and of the q field (slot sets of distinct nodes are
+// disjoint; an odd-parity slot set reaches one node along every axis).
+// Because the oldest unfinished tile never waits, progress is guaranteed even
+// if not all blocks are resident.  Every wait is bounded by a wall-clock limit
+// after which the kernel records ELBM_ERR_TIMEOUT in the status word and all
+// blocks return.
+#pragma once
+#include <algorithm>
+
+#include "step_kernels.cuh"
+
+namespace elbm {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// Layout of the sync words (reset by the host before every launch):
+//   [0] ticket, [1] abort flag, [2 .. 2+K) anomaly-phase completions,
+//   [2+K .. 2+2K) collide-phase completions, then 2 words per phase: (type, chunk).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait until *ctr >= target.  False if it gave up (timeout or abort).
+__device__ __forceinline__ bool wait_ge(const StepParams& p, const unsigned* ctr, unsigned target)
+{
+    if (ld_acquire(ctr) >= target) return true;
+    const unsigned long long t0 = globaltimer();
+    volatile unsigned* abort_flag = p.sync + 1;
+    while (true) {
+        __nanosleep(64);
+        if (ld_acquire(ctr) >= target) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) {
+            atomicExch(p.sync + 1, 1u);
+            atomicCAS(p.status, 0, ELBM_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+template <int D, int ST>
+__global__ void __launch_bounds__(kBlock, 2) k_pipelined(StepParams p)
+{
+    __shared__ int s_ticket;
+    __shared__ int s_ok;
+    const int K = p.nchunks, T = p.tiles_per_chunk;
+    const unsigned* done_a = p.sync + 2;
+    const unsigned* done_c = p.sync + 2 + K;
+    const unsigned* order = p.sync + 2 + 2 * K;
+    const int layer = (D == 3) ? p.plane : p.nx;
+    const int chunk_cells = p.chunk_planes * layer;
+    const long long total = (long long)p.nsteps * 2 * K * T;
+
+    while (true) {
+        if (threadIdx.x == 0) s_ticket = (int)atomicAdd(p.sync, 1u);
+        __syncthreads();
+        const long long t = s_ticket;
+        if (t >= total) break;
+        const int tile = (int)(t % T);
+        const long long ph_all = t / T;
+        const int step = (int)(ph_all / (2 * K));
+        const int ph = (int)(ph_all % (2 * K));
+        const int type = (int)order[2 * ph];  // 0 anomaly, 1 collide
+        const int c = (int)order[2 * ph + 1];
+        const int cm = (c == 0) ? K - 1 : c - 1, cp = (c == K - 1) ? 0 : c + 1;
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (type == 1) {
+                const unsigned tgt = (unsigned)(step + 1) * T;
+                ok = wait_ge(p, done_a + cm, tgt) && wait_ge(p, done_a + c, tgt) && wait_ge(p, done_a + cp, tgt);
+            } else if (step > 0) {
+                const unsigned tgt = (unsigned)step * T;
+                ok = wait_ge(p, done_c + cm, tgt) && wait_ge(p, done_c + c, tgt) && wait_ge(p, done_c + cp, tgt);
+            }
+            if (ok) __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+
+        const int parity = (p.parity + step) & 1;
+        const int c_begin = c * chunk_cells;
+        const int c_end = min(p.N, c_begin + chunk_cells);
+        const int t_begin = c_begin + tile * p.tile_cells;
+        const int t_end = min(c_end, t_begin + p.tile_cells);
+        if (type == 0) {
+            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock) {
+                const Node n = make_node<D>(p, cell);
+                float g[Lat<D>::Q];
+                if (parity == 0) gather<D, ST, 0>(p, n, g);
+                else gather<D, ST, 1>(p, n, g);
+                float drho, j[3];
+                moments<D>(p, g, drho, j);
+                const float inv_rho = 1.0f / (p.rho_ref + drho);
+#pragma unroll
+                for (int a = 0; a < D; ++a) p.q[a * p.N + cell] = anomaly(p, a, j[a], j[a] * inv_rho);
+            }
+        } else {
+            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock) {
+                if (parity == 0) collide_node<D, ST, 0>(p, cell);
+                else collide_node<D, ST, 1>(p, cell);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd((type == 0 ? p.sync + 2 : p.sync + 2 + K) + c, 1u);
+        }
+    }
+}
+
+// Largest resident grid of the pipelined kernel (blocks).
+template <int D>
+int pipelined_grid_impl(const Solver& s)
+{
+    int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipelined<D, ST>, kBlock, 0);
+    });
+    if (e != cudaSuccess) return 0;
+    return per_sm * s.num_sms;
+}
+
+// Choose the chunking and the size of the sync buffer.
+// Chunks hold enough layers for about 64k nodes, so that one phase spreads
+// over the whole GPU while L + 2 chunks of populations stay well inside L2;
+// L is chosen so that the blocks in flight (about one tile each) rarely reach
+// a tile whose dependencies are unfinished.
+template <int D>
+PipeGeom pipelined_geometry_impl(const Solver& s)
+{
+    PipeGeom g{};
+    const int layer = (D == 3) ? s.nx * s.ny : s.nx;
+    const int nlayers = (D == 3) ? s.nz : s.ny;
+    g.grid = pipelined_grid_impl<D>(s);
+    g.chunk_planes = std::max(1, std::min(nlayers, (65536 + layer - 1) / layer));
+    g.nchunks = (nlayers + g.chunk_planes - 1) / g.chunk_planes;
+    g.tile_cells = 2 * kBlock;
+    const int chunk_cells = g.chunk_planes * layer;
+    g.tiles_per_chunk = (chunk_cells + g.tile_cells - 1) / g.tile_cells;
+    const int L = (g.grid + 2 * g.tiles_per_chunk - 1) / (2 * g.tiles_per_chunk) + 1;
+    g.lookahead = (g.nchunks >= 3) ? std::max(1, std::min(L, g.nchunks - 2)) : 0;
+    g.sync_words = 2 + 2 * (size_t)g.nchunks + 4 * (size_t)g.nchunks;
+    return g;
+}
+
+template <int D>
+cudaError_t step_pipelined_impl(const Solver& s, int parity, int nsteps, long long* launches)
+{
+    const PipeGeom& g = s.pipe;
+    if (g.grid <= 0 || s.sync == nullptr) return cudaErrorInvalidConfiguration;
+    StepParams p;
+    fill_params(s, p);
+    p.parity = parity;
+    p.chunk_planes = g.chunk_planes;
+    p.nchunks = g.nchunks;
+    p.tile_cells = g.tile_cells;
+    p.tiles_per_chunk = g.tiles_per_chunk;
+    p.nsteps = nsteps;
+    p.lookahead = g.lookahead;
+    cudaError_t e = cudaMemsetAsync(s.sync, 0, (2 + 2 * (size_t)g.nchunks) * sizeof(unsigned), s.stream);
+    if (e != cudaSuccess) return e;
+    ELBM_DISPATCH_STORAGE(s.storage, { k_pipelined<D, ST><<<g.grid, kBlock, 0, s.stream>>>(p); });
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace elbm

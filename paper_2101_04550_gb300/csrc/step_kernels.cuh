@@ -1,0 +1,382 @@
+// Kernels of the extended LBGK step and its utilities, templated on the
+// lattice dimension D, the storage mode ST and (for the hot kernels) the AA
+// streaming parity PAR.  Included by one translation unit per lattice.
+#pragma once
+#include <cfloat>
+
+#include "lbm_device.cuh"
+
+namespace elbm {
+
+constexpr int kBlock = 256;
+
+#define ELBM_DISPATCH_STORAGE(storage, ...)                              \
+    switch (storage) {                                                   \
+        case ELBM_F32: { constexpr int ST = ELBM_F32; __VA_ARGS__; } break;             \
+        case ELBM_F32_SHIFT: { constexpr int ST = ELBM_F32_SHIFT; __VA_ARGS__; } break; \
+        case ELBM_F16_SHIFT: { constexpr int ST = ELBM_F16_SHIFT; __VA_ARGS__; } break; \
+        case ELBM_BF16_SHIFT: { constexpr int ST = ELBM_BF16_SHIFT; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;                           \
+    }
+
+// ---------------------------------------------------------------- two-pass
+// Pass 1: post-streaming moments of every node -> anomaly field q[a][cell]
+// (Eqs. density, momentum, Deviation).  Reads the populations only.
+template <int D, int ST, int PAR>
+__global__ void __launch_bounds__(kBlock) k_anomaly(StepParams p)
+{
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    const Node n = make_node<D>(p, cell);
+    float g[Lat<D>::Q];
+    gather<D, ST, PAR>(p, n, g);
+    float drho, j[3];
+    moments<D>(p, g, drho, j);
+    const float inv_rho = 1.0f / (p.rho_ref + drho);
+#pragma unroll
+    for (int a = 0; a < D; ++a) p.q[a * p.N + cell] = anomaly(p, a, j[a], j[a] * inv_rho);
+}
+
+// The per-node update once the anomaly field of this time level is complete:
+// central difference of q along each axis (Eq. Paastar1), extended
+// equilibrium, relaxation, write-back in place.
+template <int D, int ST, int PAR>
+__device__ __forceinline__ void collide_node(const StepParams& p, int cell)
+{
+    const Node n = make_node<D>(p, cell);
+    float g[Lat<D>::Q];
+    gather<D, ST, PAR>(p, n, g);
+    float drho, j[3];
+    moments<D>(p, g, drho, j);
+    float d[3] = {0.f, 0.f, 0.f};
+    if (p.eq_mode == 0) {
+        const float* q = p.q;
+        d[0] = (q[n.at(1, 0, 0)] - q[n.at(-1, 0, 0)]) * p.inv_2lam[0];
+        d[1] = (q[p.N + n.at(0, 1, 0)] - q[p.N + n.at(0, -1, 0)]) * p.inv_2lam[1];
+        if (D == 3) d[2] = (q[2 * p.N + n.at(0, 0, 1)] - q[2 * p.N + n.at(0, 0, -1)]) * p.inv_2lam[2];
+    }
+    relax<D>(p, g, drho, j, d);
+    scatter<D, ST, PAR>(p, n, g);
+}
+
+// Pass 2 over every node.
+template <int D, int ST, int PAR>
+__global__ void __launch_bounds__(kBlock) k_collide(StepParams p)
+{
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    collide_node<D, ST, PAR>(p, cell);
+}
+
+template <int D>
+cudaError_t step_two_pass_impl(const Solver& s, int parity, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    p.parity = parity;
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        if (parity == 0) {
+            if (p.eq_mode == 0) { k_anomaly<D, ST, 0><<<grid, kBlock, 0, s.stream>>>(p); ++*launches; }
+            k_collide<D, ST, 0><<<grid, kBlock, 0, s.stream>>>(p);
+        } else {
+            if (p.eq_mode == 0) { k_anomaly<D, ST, 1><<<grid, kBlock, 0, s.stream>>>(p); ++*launches; }
+            k_collide<D, ST, 1><<<grid, kBlock, 0, s.stream>>>(p);
+        }
+        ++*launches;
+    });
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- init
+// f_i = rho Psi_i(u, T + u^2, lam) (Eq. 27eq) at every node, written to the
+// even-parity slots.
+template <int D, int ST, typename TIn>
+__global__ void __launch_bounds__(kBlock) k_init(StepParams p, const TIn* rho, const TIn* u)
+{
+    using S = Storage<ST>;
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    const float drho = (float)((double)rho[cell] - (double)p.rho_ref);
+    float uu[3], dP[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        uu[a] = (float)u[(size_t)a * p.N + cell];
+        dP[a] = uu[a] * uu[a];
+    }
+    typename S::T* f = static_cast<typename S::T*>(p.f);
+    for_each_equilibrium<D>(p, drho, uu, dP, [&](int i, float geq) {
+        S::store(f + i * p.N + cell, S::shifted ? geq : geq + p.w[i] * p.rho_ref);
+    });
+}
+
+template <int D>
+cudaError_t init_impl(const Solver& s, const void* rho, const void* u, int dtype, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        if (dtype == ELBM_DTYPE_F64)
+            k_init<D, ST, double><<<grid, kBlock, 0, s.stream>>>(p, (const double*)rho, (const double*)u);
+        else
+            k_init<D, ST, float><<<grid, kBlock, 0, s.stream>>>(p, (const float*)rho, (const float*)u);
+        ++*launches;
+    });
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- read-outs
+// Post-streaming population i of a node, as a deviation g_i, at the solver's
+// current parity (not a hot path: parity is a run-time value here).
+template <int D, int ST>
+__device__ __forceinline__ double load_dev(const StepParams& p, const Node& n, int i)
+{
+    using S = Storage<ST>;
+    const typename S::T* f = static_cast<const typename S::T*>(p.f);
+    const float v = S::load(f + read_slot<D>(n, p.N, i, p.parity));
+    return S::shifted ? (double)v : (double)v - (double)p.w[i] * (double)p.rho_ref;
+}
+
+// rho and u of every node (Eqs. density, momentum), summed in FP64;
+// with a body force u is reported at the half step, u + g/2.
+template <int D, int ST, typename TOut>
+__global__ void __launch_bounds__(kBlock) k_moments(StepParams p, TOut* rho, TOut* u)
+{
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    const Node n = make_node<D>(p, cell);
+    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const double v = load_dev<D, ST>(p, n, i);
+        r += v;
+        jx += cx_of(i) * v;
+        jy += cy_of(i) * v;
+        jz += cz_of<D>(i) * v;
+    }
+    r += (double)p.rho_ref;
+    rho[cell] = (TOut)r;
+    const double j[3] = {jx * p.lam[0], jy * p.lam[1], jz * p.lam[2]};
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[(size_t)a * p.N + cell] = (TOut)(j[a] / r + 0.5 * (double)p.g[a]);
+}
+
+template <int D>
+cudaError_t moments_impl(const Solver& s, void* rho, void* u, int dtype, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        if (dtype == ELBM_DTYPE_F64)
+            k_moments<D, ST, double><<<grid, kBlock, 0, s.stream>>>(p, (double*)rho, (double*)u);
+        else
+            k_moments<D, ST, float><<<grid, kBlock, 0, s.stream>>>(p, (float*)rho, (float*)u);
+        ++*launches;
+    });
+    return cudaGetLastError();
+}
+
+// Unshifted post-streaming populations f_i = g_i + w_i rho_ref, layout f[i][cell].
+template <int D, int ST, typename TOut>
+__global__ void __launch_bounds__(kBlock) k_get_f(StepParams p, TOut* out)
+{
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    const Node n = make_node<D>(p, cell);
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i)
+        out[(size_t)i * p.N + cell] = (TOut)(load_dev<D, ST>(p, n, i) + (double)p.w[i] * (double)p.rho_ref);
+}
+
+// Store caller populations at the even-parity slots.
+template <int D, int ST, typename TIn>
+__global__ void __launch_bounds__(kBlock) k_set_f(StepParams p, const TIn* in)
+{
+    using S = Storage<ST>;
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    typename S::T* f = static_cast<typename S::T*>(p.f);
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const double v = (double)in[(size_t)i * p.N + cell];
+        const double stored = S::shifted ? v - (double)p.w[i] * (double)p.rho_ref : v;
+        S::store(f + i * p.N + cell, (float)stored);
+    }
+}
+
+template <int D>
+cudaError_t get_populations_impl(const Solver& s, void* f, int dtype, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        if (dtype == ELBM_DTYPE_F64) k_get_f<D, ST, double><<<grid, kBlock, 0, s.stream>>>(p, (double*)f);
+        else k_get_f<D, ST, float><<<grid, kBlock, 0, s.stream>>>(p, (float*)f);
+        ++*launches;
+    });
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t set_populations_impl(const Solver& s, const void* f, int dtype, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        if (dtype == ELBM_DTYPE_F64) k_set_f<D, ST, double><<<grid, kBlock, 0, s.stream>>>(p, (const double*)f);
+        else k_set_f<D, ST, float><<<grid, kBlock, 0, s.stream>>>(p, (const float*)f);
+        ++*launches;
+    });
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- FP64 diagnostics
+// Stage 1: per node rho, u (FP32) and min_i f_i into scratch mom[5][N].
+template <int D, int ST>
+__global__ void __launch_bounds__(kBlock) k_red_nodes(StepParams p, float* mom)
+{
+    const int cell = blockIdx.x * kBlock + threadIdx.x;
+    if (cell >= p.N) return;
+    const Node n = make_node<D>(p, cell);
+    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, fmin = DBL_MAX;
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const double v = load_dev<D, ST>(p, n, i);
+        r += v;
+        jx += cx_of(i) * v;
+        jy += cy_of(i) * v;
+        jz += cz_of<D>(i) * v;
+        fmin = fmin < v + (double)p.w[i] * p.rho_ref ? fmin : v + (double)p.w[i] * p.rho_ref;
+    }
+    r += (double)p.rho_ref;
+    mom[cell] = (float)r;
+    mom[(size_t)p.N + cell] = (float)(jx * p.lam[0] / r + 0.5 * (double)p.g[0]);
+    mom[(size_t)2 * p.N + cell] = (float)(jy * p.lam[1] / r + 0.5 * (double)p.g[1]);
+    mom[(size_t)3 * p.N + cell] = (D == 3) ? (float)(jz * p.lam[2] / r + 0.5 * (double)p.g[2]) : 0.f;
+    mom[(size_t)4 * p.N + cell] = (float)fmin;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce ELBM_NRED FP64 accumulators over a block: warp shuffles, then one
+// shared-memory stage across the block's warps.  Result valid in thread 0.
+__device__ __forceinline__ void block_reduce(double* acc, double* out)
+{
+    __shared__ double sh[kBlock / 32][ELBM_NRED];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < ELBM_NRED; ++k) {
+        const double v = (k == 9) ? warp_min(acc[k]) : (k == 11) ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < ELBM_NRED) {
+        const int k = threadIdx.x;
+        double v = sh[0][k];
+        for (int w = 1; w < kBlock / 32; ++w)
+            v = (k == 9) ? fmin(v, sh[w][k]) : (k == 11) ? fmax(v, sh[w][k]) : v + sh[w][k];
+        out[k] = v;
+    }
+}
+
+// Stage 2: per-block FP64 partial sums (grid-stride over nodes); vorticity and
+// d_x u_x by central differences with node spacing lam.
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* mom, double* partials)
+{
+    double acc[ELBM_NRED];
+#pragma unroll
+    for (int k = 0; k < ELBM_NRED; ++k) acc[k] = 0.0;
+    acc[9] = DBL_MAX;
+    acc[11] = 0.0;
+    const float* ux = mom + p.N;
+    const float* uy = mom + 2 * (size_t)p.N;
+    const float* uz = mom + 3 * (size_t)p.N;
+    for (int cell = blockIdx.x * kBlock + threadIdx.x; cell < p.N; cell += gridDim.x * kBlock) {
+        const Node n = make_node<D>(p, cell);
+        const double r = mom[cell];
+        const double u0 = ux[cell], u1 = uy[cell], u2 = uz[cell];
+        const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+        const bool finite = isfinite(r) && isfinite(uu);
+        acc[0] += r;
+        acc[1] += r * u0;
+        acc[2] += r * u1;
+        acc[3] += r * u2;
+        acc[4] += r * uu;
+        acc[5] += uu;
+        const double ix = 0.5 / p.lam[0], iy = 0.5 / p.lam[1], iz = 0.5 / p.lam[2];
+        const double dxuy = ((double)uy[n.at(1, 0, 0)] - uy[n.at(-1, 0, 0)]) * ix;
+        const double dyux = ((double)ux[n.at(0, 1, 0)] - ux[n.at(0, -1, 0)]) * iy;
+        double w2 = (dxuy - dyux) * (dxuy - dyux);
+        if (D == 3) {
+            const double dyuz = ((double)uz[n.at(0, 1, 0)] - uz[n.at(0, -1, 0)]) * iy;
+            const double dzuy = ((double)uy[n.at(0, 0, 1)] - uy[n.at(0, 0, -1)]) * iz;
+            const double dzux = ((double)ux[n.at(0, 0, 1)] - ux[n.at(0, 0, -1)]) * iz;
+            const double dxuz = ((double)uz[n.at(1, 0, 0)] - uz[n.at(-1, 0, 0)]) * ix;
+            w2 += (dyuz - dzuy) * (dyuz - dzuy) + (dzux - dxuz) * (dzux - dxuz);
+        }
+        acc[6] += w2;
+        const double dxux = ((double)ux[n.at(1, 0, 0)] - ux[n.at(-1, 0, 0)]) * ix;
+        acc[7] += dxux * dxux;
+        acc[8] += u0 * u0;
+        acc[9] = fmin(acc[9], (double)mom[4 * (size_t)p.N + cell]);
+        acc[10] += finite ? 0.0 : 1.0;
+        acc[11] = fmax(acc[11], finite ? sqrt(uu) : 0.0);
+    }
+    block_reduce(acc, partials + (size_t)blockIdx.x * ELBM_NRED);
+}
+
+// Stage 3: one block folds the partials in a fixed order (deterministic).
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_red_final(const double* partials, int nblocks, double* out)
+{
+    double acc[ELBM_NRED];
+#pragma unroll
+    for (int k = 0; k < ELBM_NRED; ++k) acc[k] = 0.0;
+    acc[9] = DBL_MAX;
+    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
+        const double* q = partials + (size_t)b * ELBM_NRED;
+#pragma unroll
+        for (int k = 0; k < ELBM_NRED; ++k)
+            acc[k] = (k == 9) ? fmin(acc[k], q[k]) : (k == 11) ? fmax(acc[k], q[k]) : acc[k] + q[k];
+    }
+    block_reduce(acc, out);
+}
+
+template <int D>
+cudaError_t reduce_impl(const Solver& s, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        k_red_nodes<D, ST><<<grid, kBlock, 0, s.stream>>>(p, s.mom);
+    });
+    k_red_sum<D><<<s.red_blocks, kBlock, 0, s.stream>>>(p, s.mom, s.partials);
+    k_red_final<D><<<1, kBlock, 0, s.stream>>>(s.partials, s.red_blocks, s.red_out);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace elbm

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated for the path): relative L-infinity on the velocity,
+max|u_gpu - u_oracle| / max|u_oracle|, <= 1e-5 for FP32 storage and <= 2e-3
+for FP16 shifted storage after up to 1000 steps.  BF16 shifted storage keeps
+8 mantissa bits and is held to a looser 2e-2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2101_04550_gb300 import elbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {elbm.F32: 1e-5, elbm.F32_SHIFT: 1e-5, elbm.F16_SHIFT: 2e-3, elbm.BF16_SHIFT: 2e-2}
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def run_gpu(lattice, n, lam, T, nu, rho, u, steps, storage=elbm.F32, kernel=1, equilibrium=0,
+            chunked=None):
+    with elbm.Solver(lattice, n, stretch=lam, T=T, nu=nu, storage=storage, kernel=kernel,
+                     equilibrium=equilibrium) as s:
+        s.init(rho, u)
+        if chunked:
+            for k in chunked:
+                s.step(k)
+        else:
+            s.step(steps)
+        s.sync()
+        return s.moments()
+
+
+def run_oracle(D, n, lam, T, nu, rho, u, steps, mode=oracle.EXTENDED):
+    o = oracle.Oracle(D, n, lam=tuple(lam) + (1.0,) * (3 - len(lam)), T=T, nu=nu, mode=mode)
+    o.init(rho, u)
+    o.step(steps)
+    return o.macros()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    elbm.load()
+
+
+# ------------------------------------------------------------ D2Q9 cases
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT])
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_d2q9_shear_wave_64_1000_steps(storage, kernel):
+    """D2Q9 advected shear wave, 64x64 periodic, T = 1/3, u_x = 0.1,
+    u_y = 1e-3 sin(2 pi x / 64), nu = 0.01, 1000 steps."""
+    n = (64, 64)
+    rho, u, _, _ = inputs.shear_wave(n, (1.0, 1.0), (1, 0), (0, 1), 1e-3, 0.1)
+    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, kernel)
+    _, uo = run_oracle(2, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000)
+    assert rel_linf(ug, uo) <= TOL[storage]
+    # the perturbation alone (uniform advection cannot hide an error)
+    assert rel_linf(ug[1], uo[1]) <= 20 * TOL[storage]
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("T", [1 / 3, 0.5])
+def test_d2q9_rotated_stretched_correction_active(kernel, T):
+    """Rotated wave on a lam_x = 2 lattice: the central-difference correction
+    is large here (Fig. 3)."""
+    n, lam = (32, 64), (2.0, 1.0)
+    rho, u, _, _ = inputs.shear_wave(n, lam, (1, 1), (-1, 1), 1e-3, 0.1)
+    _, ug = run_gpu(elbm.D2Q9, n, lam, T, 0.01, rho, u, 1000, elbm.F32_SHIFT, kernel)
+    _, uo = run_oracle(2, n, lam, T, 0.01, rho, u, 1000)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+def test_d2q9_double_shear_layer_128():
+    """Double shear layer (Sec. III.C) at 128x64, lam_y = 2, T = 0.5, 300 steps."""
+    n, lam = (128, 64), (1.0, 2.0)
+    rho, u = inputs.double_shear_layer(n, U=0.1)
+    _, ug = run_gpu(elbm.D2Q9, n, lam, 0.5, 0.002, rho, u, 300, elbm.F32_SHIFT, 2)
+    _, uo = run_oracle(2, n, lam, 0.5, 0.002, rho, u, 300)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+def test_d2q9_product_form_mode():
+    """Correction switched off: the product-form equilibrium of Eq. 27eq."""
+    n, lam = (32, 64), (2.0, 1.0)
+    rho, u, _, _ = inputs.shear_wave(n, lam, (1, 1), (-1, 1), 1e-3, 0.1)
+    _, ug = run_gpu(elbm.D2Q9, n, lam, 1 / 3, 0.01, rho, u, 500, elbm.F32_SHIFT, 1, equilibrium=1)
+    _, uo = run_oracle(2, n, lam, 1 / 3, 0.01, rho, u, 500, mode=oracle.PRODUCT)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", [elbm.F16_SHIFT, elbm.BF16_SHIFT])
+def test_d2q9_half_storage(storage):
+    n = (64, 64)
+    rho, u, _, _ = inputs.shear_wave(n, (1.0, 1.0), (1, 1), (-1, 1), 1e-2, 0.1)
+    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, 1)
+    _, uo = run_oracle(2, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000)
+    assert rel_linf(ug, uo) <= TOL[storage]
+
+
+# ----------------------------------------------------------- D3Q27 cases
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_d3q27_turbulence_ragged_stretched(kernel):
+    """Seeded solenoidal field on a ragged 37x20x23 grid, lam = (1, 1.5, 2), T = 0.5."""
+    n, lam = (37, 20, 23), (1.0, 1.5, 2.0)
+    rho, u = inputs.isotropic_turbulence(n, seed=1, k0=3.0, u_rms=0.05)
+    _, ug = run_gpu(elbm.D3Q27, n, lam, 0.5, 0.02, rho, u, 200, elbm.F32_SHIFT, kernel)
+    _, uo = run_oracle(3, n, lam, 0.5, 0.02, rho, u, 200)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT, elbm.F16_SHIFT])
+def test_d3q27_shear_wave_1000_steps(storage):
+    n, lam = (32, 8, 16), (1.0, 1.0, 2.0)
+    rho, u, _, _ = inputs.shear_wave(n, lam, (1, 0, 1), (-1, 0, 1), 1e-2, 0.1)
+    _, ug = run_gpu(elbm.D3Q27, n, lam, 1 / 3, 0.02, rho, u, 1000, storage, 2)
+    _, uo = run_oracle(3, n, lam, 1 / 3, 0.02, rho, u, 1000)
+    assert rel_linf(ug, uo) <= TOL[storage]
+
+
+def test_d3q27_minimum_grid():
+    """Smallest grid the central difference allows: 3x3x3."""
+    n = (3, 3, 3)
+    rng = np.random.default_rng(5)
+    rho = 1.0 + 0.01 * rng.standard_normal((3, 3, 3))
+    u = 0.03 * rng.standard_normal((3, 3, 3, 3))
+    _, ug = run_gpu(elbm.D3Q27, n, (1.0, 1.0, 1.0), 1 / 3, 0.05, rho, u, 50, elbm.F32_SHIFT, 1)
+    _, uo = run_oracle(3, n, (1.0, 1.0, 1.0), 1 / 3, 0.05, rho, u, 50)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+# ---------------------------------------------------- kernels and state
+@pytest.mark.parametrize("lattice,n", [(elbm.D3Q27, (64, 64, 48)), (elbm.D3Q27, (40, 24, 3)),
+                                       (elbm.D2Q9, (300, 700)), (elbm.D2Q9, (33, 5))])
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT])
+def test_two_pass_and_pipelined_agree_bitwise(lattice, n, storage):
+    """Both kernel forms evaluate the same per-node arithmetic, so the states
+    agree bit for bit, across launches of several steps and both parities."""
+    D = 2 if lattice == elbm.D2Q9 else 3
+    if D == 3:
+        rho, u = inputs.isotropic_turbulence(n, seed=2, k0=3.0, u_rms=0.05)
+    else:
+        rho, u = inputs.double_shear_layer(n, U=0.1)
+    lam = (1.0, 2.0, 1.0)
+    outs = []
+    for kernel in (1, 2):
+        with elbm.Solver(lattice, n, stretch=lam, T=0.5, nu=0.01, storage=storage, kernel=kernel) as s:
+            s.init(rho, u)
+            for k in (1, 2, 4):
+                s.step(k)
+            outs.append(s.get_populations())
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("lattice,n", [(elbm.D2Q9, (20, 12)), (elbm.D3Q27, (9, 7, 5))])
+def test_populations_one_and_two_steps(lattice, n):
+    """Populations after init (Eq. 27eq), one (even parity) and two (odd
+    parity) steps against the oracle's, element by element."""
+    D = 2 if lattice == elbm.D2Q9 else 3
+    rng = np.random.default_rng(11)
+    shape = tuple(n[::-1])
+    rho = 1.0 + 0.01 * rng.standard_normal(shape)
+    u = 0.05 * rng.standard_normal((D,) + shape)
+    lam = (1.5, 1.0, 2.0)[:D]
+    o = oracle.Oracle(D, n, lam=tuple(lam) + (1.0,) * (3 - D), T=0.4, nu=0.03)
+    o.init(rho, u)
+    with elbm.Solver(lattice, n, stretch=lam, T=0.4, nu=0.03, storage=elbm.F32_SHIFT) as s:
+        s.init(rho, u)
+        for steps in (0, 1, 1):
+            if steps:
+                s.step(1)
+                o.step(1)
+            fg = s.get_populations().reshape(o.f.shape)
+            assert np.abs(fg - o.f).max() <= 2e-7
+
+
+def test_set_get_populations_roundtrip():
+    n = (10, 9, 8)
+    rng = np.random.default_rng(4)
+    f = 0.03 + 0.01 * rng.random((27,) + tuple(n[::-1]))
+    with elbm.Solver(elbm.D3Q27, n, T=1 / 3, nu=0.02, storage=elbm.F32) as s:
+        s.set_populations(f)
+        np.testing.assert_allclose(s.get_populations(), f, rtol=1e-7, atol=0)
+
+
+def test_reductions_fp64():
+    """elbm_reduce against numpy on the moments read back from the GPU."""
+    n, lam = (24, 20, 16), (1.0, 1.0, 2.0)
+    rho, u = inputs.isotropic_turbulence(n, seed=3, k0=3.0, u_rms=0.05)
+    with elbm.Solver(elbm.D3Q27, n, stretch=lam, T=0.5, nu=0.02, storage=elbm.F32_SHIFT) as s:
+        s.init(rho, u)
+        s.step(10)
+        r, uu = s.moments(dtype=np.float32)
+        red = s.reduce()
+        f = s.get_populations()
+    r = r.astype(np.float64)
+    uu = uu.astype(np.float64)
+    assert np.isclose(red["mass"], r.sum(), rtol=1e-9)
+    assert np.isclose(red["rho_u2"], (r * (uu ** 2).sum(0)).sum(), rtol=1e-6)
+    assert np.isclose(red["u2"], (uu ** 2).sum(), rtol=1e-6)
+    dx = lambda a, ax, h: (np.roll(a, -1, ax) - np.roll(a, 1, ax)) / (2 * h)
+    # axes of the (z, y, x) arrays: x -> 2, y -> 1, z -> 0
+    wx = dx(uu[2], 1, lam[1]) - dx(uu[1], 0, lam[2])
+    wy = dx(uu[0], 0, lam[2]) - dx(uu[2], 2, lam[0])
+    wz = dx(uu[1], 2, lam[0]) - dx(uu[0], 1, lam[1])
+    assert np.isclose(red["curl2"], (wx ** 2 + wy ** 2 + wz ** 2).sum(), rtol=1e-5)
+    assert np.isclose(red["dxux2"], (dx(uu[0], 2, lam[0]) ** 2).sum(), rtol=1e-5)
+    assert np.isclose(red["fmin"], f.min(), rtol=1e-6)
+    assert red["nonfinite"] == 0
+    assert np.isclose(red["umax"], np.sqrt((uu ** 2).sum(0)).max(), rtol=1e-6)
+
+
+def test_mass_momentum_conserved_on_gpu():
+    n = (32, 32, 32)
+    rho, u = inputs.isotropic_turbulence(n, seed=4, k0=4.0, u_rms=0.08)
+    with elbm.Solver(elbm.D3Q27, n, T=0.5, nu=0.02, storage=elbm.F32_SHIFT, kernel=2) as s:
+        s.init(rho, u)
+        r0 = s.reduce()
+        s.step(500)
+        r1 = s.reduce()
+    assert abs(r1["mass"] - r0["mass"]) / r0["mass"] < 1e-6
+    for k in ("mom_x", "mom_y", "mom_z"):
+        assert abs(r1[k] - r0[k]) / r0["mass"] < 1e-7
