@@ -53,8 +53,9 @@ extern "C" {
 /* --------------------------------------------------------- storage of f_i */
 /* Collision arithmetic is FP32 in every mode.  "SHIFT" modes store
  * g_i = f_i - w_i rho_ref with w_i = Psi_i(0, T, lam) the rest equilibrium at the
- * run's T and stretch (rho_ref = 1 unless set by ELBM_OPT_RHO_REF before init);
- * half-precision stores round to nearest even. */
+ * run's T and stretch (rho_ref = 1 unless set by ELBM_OPT_RHO_REF before init;
+ * see ELBM_OPT_U_REF_* for a moving baseline); half-precision stores round to
+ * nearest even. */
 #define ELBM_F32         0  /* f_i as float                       (4 B/population) */
 #define ELBM_F16_SHIFT   1  /* g_i as IEEE half                   (2 B/population) */
 #define ELBM_BF16_SHIFT  2  /* g_i as bfloat16                    (2 B/population) */
@@ -70,7 +71,9 @@ extern "C" {
  *   2 = product form truncated to second order in u (Sec. III preamble). */
 #define ELBM_OPT_EQUILIBRIUM 1
 /* ELBM_OPT_KERNEL: 0 = automatic; 1 = two-pass (anomaly pass, collide pass);
- *   2 = persistent pipelined pass (same arithmetic, one cooperative launch per step). */
+ *   2 = pipelined pass (same arithmetic; one launch per step whose tiles are
+ *   handed out by an atomic ticket so that the collide phase re-reads the
+ *   populations from L2). */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3
@@ -83,6 +86,18 @@ extern "C" {
  *   y = ny-1 (periodic otherwise); the anomaly's ghost value beyond a wall is
  *   the negated value of the wall-adjacent node. */
 #define ELBM_OPT_WALLS_Y     7
+/* ELBM_OPT_U_REF_X/Y/Z: velocity U0 of the storage baseline of the SHIFT modes
+ *   (before init).  Stored values are g_i = f_i - rho_ref b_i with
+ *   b_i = Psi_i(U0, T + U0^2, lam), the product-form equilibrium of (rho_ref, U0)
+ *   (Eqs. prod, 27eq); U0 = 0 (the default) gives the rest weights w_i.  A U0
+ *   near the flow's mean velocity shrinks the stored values and so the
+ *   rounding error of half-precision storage.  Ignored by ELBM_F32. */
+#define ELBM_OPT_U_REF_X     8
+#define ELBM_OPT_U_REF_Y     9
+#define ELBM_OPT_U_REF_Z    10
+/* ELBM_OPT_U_REF_AUTO: 1 = at elbm_init set U0 to the mean velocity
+ *   sum(rho u) / sum(rho) of the given field (conserved on periodic grids). */
+#define ELBM_OPT_U_REF_AUTO 11
 
 /* ------------------------------------------------------- diagnostics */
 /* elbm_reduce output, all accumulated in FP64 over every node (sums, not means):
@@ -158,6 +173,9 @@ double elbm_omega(const elbm_solver* s);
 long long elbm_device_bytes(const elbm_solver* s);
 /* Number of kernel launches this solver has issued since creation. */
 long long elbm_launch_count(const elbm_solver* s);
+
+/* Baseline velocity U0 of the shifted storage in use, out[3] (zeros for ELBM_F32). */
+int elbm_get_u_ref(const elbm_solver* s, double* out);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* elbm_last_error(void);

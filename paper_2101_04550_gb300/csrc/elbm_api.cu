@@ -34,6 +34,8 @@ constexpr int kStepsPerLaunch = 256;  // bound on the duration of one pipelined 
 
 namespace elbm {
 
+bool base_triplet(double T, double lam, double U0, float out[3], double* u0_eff);
+
 size_t storage_bytes(int storage)
 {
     return (storage == ELBM_F16_SHIFT || storage == ELBM_BF16_SHIFT) ? 2 : 4;
@@ -54,6 +56,26 @@ static void rest_triplet(double T, double lam, float out[3])
     out[2] = (float)side;
     out[1] = (float)centre;
 }
+
+// Storage-baseline triplet per axis, Psi_c(U0, T + U0^2, lam), rounded so that
+// the three floats sum to exactly one (centre a multiple of 2^-24, sides
+// multiples of 2^-25).  Returns false if a value is not positive.  *u0_eff
+// receives the velocity the rounded triplet carries, lam (b_+ - b_-).
+bool base_triplet(double T, double lam, double U0, float out[3], double* u0_eff)
+{
+    const double P0 = T + U0 * U0;
+    const double centre = std::nearbyint((1.0 - P0 / (lam * lam)) * 16777216.0) / 16777216.0;
+    const double sides = 1.0 - centre;
+    const double plus = std::nearbyint((0.5 * sides + 0.5 * U0 / lam) * 33554432.0) / 33554432.0;
+    const double minus = sides - plus;
+    out[0] = (float)minus;
+    out[1] = (float)centre;
+    out[2] = (float)plus;
+    *u0_eff = lam * (plus - minus);
+    return minus > 0.0 && centre > 0.0 && plus > 0.0;
+}
+
+static bool shifted_storage(int storage) { return storage != ELBM_F32; }
 
 void fill_params(const Solver& s, StepParams& p)
 {
@@ -77,11 +99,22 @@ void fill_params(const Solver& s, StepParams& p)
         rest_triplet(s.T, l, p.rest[a]);
         p.inv_theta[a] = (float)(1.0 / (2.0 * (double)p.rest[a][0]));
     }
+    for (int a = 0; a < 3; ++a) {
+        const double U0 = (a < s.D && shifted_storage(s.storage)) ? s.u_ref[a] : 0.0;
+        double u0_eff = 0.0;
+        base_triplet(s.T, s.lam[a], U0, p.base[a], &u0_eff);
+        p.u0[a] = (float)u0_eff;
+        p.j0[a] = (float)(s.rho_ref * u0_eff);
+    }
     for (int i = 0; i < s.Q; ++i) {
         const int c[3] = {i % 3, (i / 3) % 3, i / 9};
-        double w = 1.0;
-        for (int a = 0; a < s.D; ++a) w *= (double)p.rest[a][c[a]];
+        double w = 1.0, b = 1.0;
+        for (int a = 0; a < s.D; ++a) {
+            w *= (double)p.rest[a][c[a]];
+            b *= (double)p.base[a][c[a]];
+        }
         p.w[i] = (float)w;
+        p.bw[i] = (float)b;
     }
     p.T = (float)s.T;
     p.omega = (float)s.omega;
@@ -144,6 +177,8 @@ int check_status(elbm_solver* s)
 }
 
 bool pipelined_usable(const elbm_solver* s) { return s->pipe.grid > 0 && s->sync != nullptr; }
+
+bool shifted_storage_mode(int storage) { return storage != ELBM_F32; }
 
 }  // namespace
 
@@ -254,6 +289,26 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             if (s->initialised) return fail(ELBM_ERR_STATE, "rho_ref must be set before init");
             s->rho_ref = value;
             return ELBM_OK;
+        case ELBM_OPT_U_REF_X:
+        case ELBM_OPT_U_REF_Y:
+        case ELBM_OPT_U_REF_Z: {
+            const int a = key - ELBM_OPT_U_REF_X;
+            if (!std::isfinite(value)) return fail(ELBM_ERR_ARG, "baseline velocity must be finite");
+            if (s->initialised) return fail(ELBM_ERR_STATE, "the baseline velocity must be set before init");
+            if (a >= s->D) return value == 0.0 ? ELBM_OK : fail(ELBM_ERR_ARG, "no such axis for this lattice");
+            float tri[3];
+            double ueff;
+            if (!elbm::base_triplet(s->T, s->lam[a], value, tri, &ueff))
+                return fail(ELBM_ERR_UNREALIZABLE, "baseline velocity %g gives a non-positive baseline population", value);
+            s->u_ref[a] = value;
+            s->u_ref_auto = 0;
+            return ELBM_OK;
+        }
+        case ELBM_OPT_U_REF_AUTO:
+            if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "u_ref_auto must be 0 or 1");
+            if (s->initialised) return fail(ELBM_ERR_STATE, "the baseline velocity must be set before init");
+            s->u_ref_auto = (int)value;
+            return ELBM_OK;
         case ELBM_OPT_FORCE_X:
         case ELBM_OPT_FORCE_Y:
         case ELBM_OPT_FORCE_Z:
@@ -264,6 +319,8 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             return fail(ELBM_ERR_ARG, "unknown option %d", key);
     }
 }
+
+static cudaError_t ensure_reduce_scratch(elbm_solver* s);
 
 static cudaError_t stage_to_device(const void* host, size_t bytes, void** dev, cudaStream_t st)
 {
@@ -286,6 +343,24 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
         if (e == cudaSuccess) e = stage_to_device(u, es * s->D * s->N, &t2, s->stream);
         drho = t1;
         du = t2;
+    }
+    if (e == cudaSuccess && s->u_ref_auto && shifted_storage_mode(s->storage)) {
+        // baseline velocity = mean velocity sum(rho u)/sum(rho) of the given field
+        e = ensure_reduce_scratch(s);
+        if (e == cudaSuccess)
+            e = (s->D == 2) ? elbm::field_sums_impl<2>(*s, drho, du, dtype, &s->launches)
+                            : elbm::field_sums_impl<3>(*s, drho, du, dtype, &s->launches);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->host_red, s->red_out, sizeof(double) * ELBM_NRED, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) {
+            for (int a = 0; a < s->D; ++a) {
+                const double U0 = s->host_red[1 + a] / s->host_red[0];
+                float tri[3];
+                double ueff;
+                s->u_ref[a] = (std::isfinite(U0) && elbm::base_triplet(s->T, s->lam[a], U0, tri, &ueff)) ? U0 : 0.0;
+            }
+        }
     }
     if (e == cudaSuccess)
         e = (s->D == 2) ? elbm::init_impl<2>(*s, drho, du, dtype, &s->launches)
@@ -411,10 +486,8 @@ int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device
     return ELBM_OK;
 }
 
-int elbm_reduce(elbm_solver* s, double* out)
+static cudaError_t ensure_reduce_scratch(elbm_solver* s)
 {
-    if (!s || !out) return fail(ELBM_ERR_ARG, "NULL argument");
-    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_reduce before init");
     cudaError_t e = cudaSuccess;
     if (!s->mom) {
         s->red_blocks = std::max(1, std::min(8 * s->num_sms, (int)((s->N + 255) / 256)));
@@ -427,10 +500,19 @@ int elbm_reduce(elbm_solver* s, double* out)
             cudaFree(s->red_out);
             s->mom = nullptr;
             s->partials = s->red_out = nullptr;
-            return cuda_fail(e, "elbm_reduce scratch");
+            return e;
         }
         s->bytes += 5 * sizeof(float) * (size_t)s->N + sizeof(double) * ELBM_NRED * (s->red_blocks + 1);
     }
+    return e;
+}
+
+int elbm_reduce(elbm_solver* s, double* out)
+{
+    if (!s || !out) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_reduce before init");
+    cudaError_t e = ensure_reduce_scratch(s);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_reduce scratch");
     e = (s->D == 2) ? elbm::reduce_impl<2>(*s, &s->launches) : elbm::reduce_impl<3>(*s, &s->launches);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->host_red, s->red_out, sizeof(double) * ELBM_NRED, cudaMemcpyDeviceToHost, s->stream);
@@ -448,5 +530,12 @@ long long elbm_steps_done(const elbm_solver* s) { return s ? s->steps_done : 0; 
 double elbm_omega(const elbm_solver* s) { return s ? s->omega : 0.0; }
 long long elbm_device_bytes(const elbm_solver* s) { return s ? (long long)s->bytes : 0; }
 long long elbm_launch_count(const elbm_solver* s) { return s ? s->launches : 0; }
+
+int elbm_get_u_ref(const elbm_solver* s, double* out)
+{
+    if (!s || !out) return fail(ELBM_ERR_ARG, "NULL argument");
+    for (int a = 0; a < 3; ++a) out[a] = (a < s->D && shifted_storage_mode(s->storage)) ? s->u_ref[a] : 0.0;
+    return ELBM_OK;
+}
 
 }  // extern "C"

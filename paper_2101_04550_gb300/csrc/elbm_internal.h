@@ -28,8 +28,12 @@ struct StepParams {
     float inv_2lam[3];    // 1/(2 lam_a): central-difference weight (node spacing lam_a)
     float lam2m3T[3];     // lam_a^2 - 3T
     float rest[3][3];     // rest triplet per axis: Psi_c(0, T, lam_a), index c+1
-    float w[kMaxQ];       // rest weights w_i = prod_a rest[a][c_ia+1]
+    float w[kMaxQ];       // rest weights w_i = prod_a rest[a][c_ia+1] (conservation projection)
     float inv_theta[3];   // 1 / sum_i w_i c_ia^2 = 1 / (2 rest[a][0])
+    float base[3][3];     // storage baseline triplet per axis: Psi_c(U0_a, T + U0_a^2, lam_a)
+    float bw[kMaxQ];      // storage baseline b_i = prod_a base[a][c_ia+1]; stored g_i = f_i - rho_ref b_i
+    float u0[3];          // baseline velocity U0 (zero unless set)
+    float j0[3];          // rho_ref U0: baseline momentum
     float T;              // temperature (R = 1)
     float omega;          // relaxation frequency
     float coef;           // (2 - omega) / (2 omega)
@@ -66,6 +70,8 @@ struct Solver {
     double lam[3] = {1, 1, 1};
     double T = 0, nu = 0, omega = 0, rho_ref = 1.0;
     double g[3] = {0, 0, 0};
+    double u_ref[3] = {0, 0, 0};   // storage baseline velocity U0 (shifted storage modes)
+    int u_ref_auto = 0;            // 1: U0 = mean velocity of the field given to elbm_init
     int eq_mode = 0;
     int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined
     int walls_y = 0;
@@ -103,5 +109,6 @@ template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long
 template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, long long*);
 template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
+template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
 
 }  // namespace elbm

@@ -126,7 +126,7 @@ __device__ __forceinline__ void gather(const StepParams& p, const Node& n, float
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
         const float v = S::load(f + read_slot<D>(n, p.N, i, PAR));
-        g[i] = S::shifted ? v : v - p.w[i] * p.rho_ref;
+        g[i] = S::shifted ? v : v - p.bw[i] * p.rho_ref;
     }
 }
 
@@ -137,14 +137,15 @@ __device__ __forceinline__ void scatter(const StepParams& p, const Node& n, cons
     typename S::T* f = static_cast<typename S::T*>(p.f);
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
-        const float v = S::shifted ? g[i] : g[i] + p.w[i] * p.rho_ref;
+        const float v = S::shifted ? g[i] : g[i] + p.bw[i] * p.rho_ref;
         S::store(f + write_slot<D>(n, p.N, i, PAR), v);
     }
 }
 
 // ------------------------------------------------------------------ moments
-// drho = sum_i g_i (so rho = rho_ref + drho, Eq. density, since sum_i w_i = 1);
-// j_a = lam_a sum_i c_ia g_i = rho u_a (Eq. momentum, since sum_i c_i w_i = 0).
+// drho = sum_i g_i (so rho = rho_ref + drho, Eq. density, since sum_i b_i = 1);
+// j_a = rho_ref U0_a + lam_a sum_i c_ia g_i = rho u_a (Eq. momentum, since the
+// baseline b_i carries the momentum rho_ref U0).
 template <int D>
 __device__ __forceinline__ void moments(const StepParams& p, const float* g, float& drho, float* j)
 {
@@ -160,9 +161,9 @@ __device__ __forceinline__ void moments(const StepParams& p, const float* g, flo
         if (cz_of<D>(i) == -1) sz -= g[i];
     }
     drho = r;
-    j[0] = p.lam[0] * sx;
-    j[1] = p.lam[1] * sy;
-    j[2] = (D == 3) ? p.lam[2] * sz : 0.f;
+    j[0] = fmaf(p.lam[0], sx, p.j0[0]);
+    j[1] = fmaf(p.lam[1], sy, p.j0[1]);
+    j[2] = (D == 3) ? fmaf(p.lam[2], sz, p.j0[2]) : 0.f;
 }
 
 // Diagonal anomaly Q~_aaa = rho u_a (lam_a^2 - 3T) - rho u_a^3 = j_a (lam_a^2 - 3T - u_a^2)
@@ -173,38 +174,39 @@ __device__ __forceinline__ float anomaly(const StepParams& p, int a, float ja, f
 }
 
 // ------------------------------------------------- extended equilibrium + BGK
-// Equilibrium deviation geq_i = rho Psi_i(u, P, lam) - rho_ref w_i for the
-// per-axis pressure excess dP_a = P_aa - T.  Per axis the triplet
-// (Eqs. phi0S, phiPlusS, phiMinusS) is Psi_c = rest_c + delta_c with
-// delta_0 = -dP/lam^2 and delta_{+-1} = (+-u/lam + dP/lam^2)/2, so
-//   Psi_i - w_i = sum_a (prod_{b<a} rest_b) delta_a (prod_{b>a} Psi_b)
-// is formed without cancellation, and rho Psi_i - rho_ref w_i =
-// (rho - rho_ref) Psi_i + rho_ref (Psi_i - w_i).
+// Equilibrium deviation geq_i = rho Psi_i(u, P, lam) - rho_ref b_i from the
+// storage baseline b_i = Psi_i(U0, T + U0^2, lam) (U0 = 0 gives the rest
+// equilibrium w_i).  Per axis the triplet (Eqs. phi0S, phiPlusS, phiMinusS) is
+// Psi_c = base_c + delta_c with, for du = u - U0 and dP = P - (T + U0^2),
+// delta_0 = -dP/lam^2 and delta_{+-1} = (+-du/lam + dP/lam^2)/2, so
+//   Psi_i - b_i = sum_a (prod_{b<a} base_b) delta_a (prod_{b>a} Psi_b)
+// is formed without cancellation, and rho Psi_i - rho_ref b_i =
+// (rho - rho_ref) Psi_i + rho_ref (Psi_i - b_i).
 template <int D, typename F>
-__device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float drho, const float* u,
+__device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float drho, const float* du,
                                                      const float* dP, F&& fn)
 {
     float A[3][3], dl[3][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         const float s = dP[a] * p.inv_lam2[a];
-        const float t = u[a] * p.inv_lam[a];
+        const float t = du[a] * p.inv_lam[a];
         dl[a][0] = 0.5f * (s - t);
         dl[a][1] = -s;
         dl[a][2] = 0.5f * (s + t);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A[a][c] = p.rest[a][c] + dl[a][c];
+        for (int c = 0; c < 3; ++c) A[a][c] = p.base[a][c] + dl[a][c];
     }
 #pragma unroll
     for (int cy = 0; cy < 3; ++cy) {
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
             const float pxy = A[0][cx] * A[1][cy];
-            const float dxy = fmaf(dl[0][cx], A[1][cy], p.rest[0][cx] * dl[1][cy]);
+            const float dxy = fmaf(dl[0][cx], A[1][cy], p.base[0][cx] * dl[1][cy]);
             if (D == 2) {
                 fn(cx + 3 * cy, fmaf(drho, pxy, p.rho_ref * dxy));
             } else {
-                const float bxy = p.rest[0][cx] * p.rest[1][cy];
+                const float bxy = p.base[0][cx] * p.base[1][cy];
 #pragma unroll
                 for (int cz = 0; cz < 3; ++cz) {
                     const float psi = pxy * A[2][cz];
@@ -213,6 +215,19 @@ __device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float 
                 }
             }
         }
+    }
+}
+
+// Per-axis arguments of for_each_equilibrium for velocity u and pressure
+// excess over T, pex = P - T: du = u - U0, dP = pex - U0^2 = du (u + U0) + (pex - u^2).
+template <int D>
+__device__ __forceinline__ void baseline_args(const StepParams& p, const float* u, const float* corr,
+                                              float* du, float* dP)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        du[a] = u[a] - p.u0[a];
+        dP[a] = fmaf(du[a], u[a] + p.u0[a], corr[a]);
     }
 }
 
@@ -233,35 +248,35 @@ template <int D>
 __device__ __forceinline__ void relax(const StepParams& p, float* g, float drho, const float* j,
                                       const float* d)
 {
-    constexpr int Q = Lat<D>::Q;
     const float rho = p.rho_ref + drho;
     const float inv_rho = 1.0f / rho;
-    float u[3], dP[3];
+    float u[3], pcorr[3], du[3], dP[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         u[a] = j[a] * inv_rho;
-        dP[a] = fmaf(p.coef * inv_rho, d[a], u[a] * u[a]);
+        pcorr[a] = p.coef * inv_rho * d[a];
     }
-    float dlt[Q];
-    for_each_equilibrium<D>(p, drho, u, dP, [&](int i, float geq) { dlt[i] = geq - g[i]; });
+    baseline_args<D>(p, u, pcorr, du, dP);
+    // pass 1: moments of the increments (the equilibrium is recomputed in
+    // pass 2 instead of being kept, which saves Q registers per thread)
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        e0 += dlt[i];
-        if (cx_of(i) == 1) ex += dlt[i];
-        if (cx_of(i) == -1) ex -= dlt[i];
-        if (cy_of(i) == 1) ey += dlt[i];
-        if (cy_of(i) == -1) ey -= dlt[i];
-        if (cz_of<D>(i) == 1) ez += dlt[i];
-        if (cz_of<D>(i) == -1) ez -= dlt[i];
-    }
+    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
+        const float dl = geq - g[i];
+        e0 += dl;
+        if (cx_of(i) == 1) ex += dl;
+        if (cx_of(i) == -1) ex -= dl;
+        if (cy_of(i) == 1) ey += dl;
+        if (cy_of(i) == -1) ey -= dl;
+        if (cz_of<D>(i) == 1) ez += dl;
+        if (cz_of<D>(i) == -1) ez -= dl;
+    });
     const float kx = ex * p.inv_theta[0], ky = ey * p.inv_theta[1], kz = (D == 3) ? ez * p.inv_theta[2] : 0.f;
     const float om = p.omega;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float corr = p.w[i] * (e0 + cx_of(i) * kx + cy_of(i) * ky + cz_of<D>(i) * kz);
-        g[i] = fmaf(om, dlt[i] - corr, g[i]);
-    }
+    // pass 2: projected relaxation, one rounding per population
+    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
+        const float proj = p.w[i] * (e0 + cx_of(i) * kx + cy_of(i) * ky + cz_of<D>(i) * kz);
+        g[i] = fmaf(om, (geq - g[i]) - proj, g[i]);
+    });
 }
 
 }  // namespace elbm

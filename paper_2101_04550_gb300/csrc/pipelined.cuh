@@ -12,13 +12,14 @@
 //     A(K-1), A(0), ..., A(L), C(0), A(L+1), C(1), A(L+2), ...
 // so that A(c) runs L chunks ahead of C(c) and the re-read of chunk c hits L2.
 //
-// Work is split into tiles and handed out by an atomic ticket.  A tile waits
-// (bounded) only for tiles with smaller tickets:
-//   C_s(c) waits for A_s(c-1), A_s(c), A_s(c+1) to be complete, and
-//   A_s(c) (s > 0) waits for C_{s-1}(c-1), C_{s-1}(c), C_{s-1}(c+1),
-// which covers every read-after-write and write-after-read hazard of the
-// in-place slots and of the q field (slot sets of distinct nodes are
-// disjoint; an odd-parity slot set reaches one node along every axis).
+// One launch advances one time step.  Work is split into tiles and handed out
+// by an atomic ticket.  A collide tile of chunk c waits (bounded) for the
+// anomaly phases of chunks c-1, c and c+1 to be complete; with the phase order
+// above those have smaller tickets.  This covers every hazard of the in-place
+// slots and of the q field: the anomaly phase of c reads the slot set of c
+// before the collide phase of c rewrites it, slot sets of distinct nodes are
+// disjoint, and q of chunks c-1..c+1 is complete before C(c) reads it.  The
+// kernel boundary orders consecutive steps.
 // Because the oldest unfinished tile never waits, progress is guaranteed even
 // if not all blocks are resident.  Every wait is bounded by a wall-clock limit
 // after which the kernel records ELBM_ERR_TIMEOUT in the status word and all
@@ -32,14 +33,25 @@ namespace elbm {
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
-// Layout of the sync words (reset by the host before every launch):
-//   [0] ticket, [1] abort flag, [2 .. 2+K) anomaly-phase completions,
-//   [2+K .. 2+2K) collide-phase completions, then 2 words per phase: (type, chunk).
+// Resident blocks per SM the pipelined kernel is compiled for (register cap
+// 65536 / (256 * ELBM_PIPE_MIN_BLOCKS)).
+#ifndef ELBM_PIPE_MIN_BLOCKS
+#define ELBM_PIPE_MIN_BLOCKS 3
+#endif
+
+// Layout of the sync words (the first 2 + 2K are reset by the host before
+// every launch): [0] ticket, [1] abort flag, [2 .. 2+K) anomaly-phase
+// completions per chunk, [2+K .. 2+2K) collide-phase completions per chunk,
+// then 2 words per phase of the step: (type, chunk).
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -55,7 +67,7 @@ __device__ __forceinline__ bool wait_ge(const StepParams& p, const unsigned* ctr
     const unsigned long long t0 = globaltimer();
     volatile unsigned* abort_flag = p.sync + 1;
     while (true) {
-        __nanosleep(64);
+        __nanosleep(32);
         if (ld_acquire(ctr) >= target) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitLimitNs) {
@@ -66,57 +78,56 @@ __device__ __forceinline__ bool wait_ge(const StepParams& p, const unsigned* ctr
     }
 }
 
-template <int D, int ST>
-__global__ void __launch_bounds__(kBlock, 2) k_pipelined(StepParams p)
+// One time step (streaming parity PAR) over the whole grid.  Thread 0 of a
+// block fetches the next ticket while the block works on the current tile, so
+// the atomic's latency is hidden; a block holding tickets t < t' only ever
+// waits for tickets below t, so the deadlock-freedom argument is unchanged.
+template <int D, int ST, int PAR>
+__global__ void __launch_bounds__(kBlock, ELBM_PIPE_MIN_BLOCKS) k_pipelined(StepParams p)
 {
-    __shared__ int s_ticket;
+    __shared__ int s_next;
     __shared__ int s_ok;
     const int K = p.nchunks, T = p.tiles_per_chunk;
-    const unsigned* done_a = p.sync + 2;
-    const unsigned* done_c = p.sync + 2 + K;
+    unsigned* done_a = p.sync + 2;
+    unsigned* done_c = p.sync + 2 + K;
     const unsigned* order = p.sync + 2 + 2 * K;
     const int layer = (D == 3) ? p.plane : p.nx;
     const int chunk_cells = p.chunk_planes * layer;
-    const long long total = (long long)p.nsteps * 2 * K * T;
+    const int total = 2 * K * T;
 
-    while (true) {
-        if (threadIdx.x == 0) s_ticket = (int)atomicAdd(p.sync, 1u);
-        __syncthreads();
-        const long long t = s_ticket;
-        if (t >= total) break;
-        const int tile = (int)(t % T);
-        const long long ph_all = t / T;
-        const int step = (int)(ph_all / (2 * K));
-        const int ph = (int)(ph_all % (2 * K));
-        const int type = (int)order[2 * ph];  // 0 anomaly, 1 collide
+    if (threadIdx.x == 0) s_next = (int)atomicAdd(p.sync, 1u);
+    __syncthreads();
+    int t = s_next;
+    while (t < total) {
+        const int tile = t % T;
+        const int ph = t / T;
+        const int type = (int)order[2 * ph];  // 0 anomaly phase, 1 collide phase
         const int c = (int)order[2 * ph + 1];
-        const int cm = (c == 0) ? K - 1 : c - 1, cp = (c == K - 1) ? 0 : c + 1;
+        __syncthreads();  // every thread has read s_next before it is rewritten
         if (threadIdx.x == 0) {
+            s_next = (int)atomicAdd(p.sync, 1u);
             bool ok = true;
             if (type == 1) {
-                const unsigned tgt = (unsigned)(step + 1) * T;
+                const int cm = (c == 0) ? K - 1 : c - 1, cp = (c == K - 1) ? 0 : c + 1;
+                const unsigned tgt = (unsigned)T;
                 ok = wait_ge(p, done_a + cm, tgt) && wait_ge(p, done_a + c, tgt) && wait_ge(p, done_a + cp, tgt);
-            } else if (step > 0) {
-                const unsigned tgt = (unsigned)step * T;
-                ok = wait_ge(p, done_c + cm, tgt) && wait_ge(p, done_c + c, tgt) && wait_ge(p, done_c + cp, tgt);
             }
-            if (ok) __threadfence();
             s_ok = ok;
         }
         __syncthreads();
         if (!s_ok) break;
+        const int t_next = s_next;
 
-        const int parity = (p.parity + step) & 1;
         const int c_begin = c * chunk_cells;
         const int c_end = min(p.N, c_begin + chunk_cells);
         const int t_begin = c_begin + tile * p.tile_cells;
         const int t_end = min(c_end, t_begin + p.tile_cells);
         if (type == 0) {
+#pragma unroll 1
             for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock) {
                 const Node n = make_node<D>(p, cell);
                 float g[Lat<D>::Q];
-                if (parity == 0) gather<D, ST, 0>(p, n, g);
-                else gather<D, ST, 1>(p, n, g);
+                gather<D, ST, PAR>(p, n, g);
                 float drho, j[3];
                 moments<D>(p, g, drho, j);
                 const float inv_rho = 1.0f / (p.rho_ref + drho);
@@ -124,16 +135,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_pipelined(StepParams p)
                 for (int a = 0; a < D; ++a) p.q[a * p.N + cell] = anomaly(p, a, j[a], j[a] * inv_rho);
             }
         } else {
-            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock) {
-                if (parity == 0) collide_node<D, ST, 0>(p, cell);
-                else collide_node<D, ST, 1>(p, cell);
-            }
+#pragma unroll 1
+            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock)
+                collide_node<D, ST, PAR>(p, cell);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd((type == 0 ? p.sync + 2 : p.sync + 2 + K) + c, 1u);
-        }
+        if (threadIdx.x == 0) red_release_add((type == 0 ? done_a : done_c) + c, 1u);
+        t = t_next;
     }
 }
 
@@ -144,7 +152,7 @@ int pipelined_grid_impl(const Solver& s)
     int per_sm = 0;
     cudaError_t e = cudaSuccess;
     ELBM_DISPATCH_STORAGE(s.storage, {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipelined<D, ST>, kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pipelined<D, ST, 0>, kBlock, 0);
     });
     if (e != cudaSuccess) return 0;
     return per_sm * s.num_sms;
@@ -180,17 +188,22 @@ cudaError_t step_pipelined_impl(const Solver& s, int parity, int nsteps, long lo
     if (g.grid <= 0 || s.sync == nullptr) return cudaErrorInvalidConfiguration;
     StepParams p;
     fill_params(s, p);
-    p.parity = parity;
     p.chunk_planes = g.chunk_planes;
     p.nchunks = g.nchunks;
     p.tile_cells = g.tile_cells;
     p.tiles_per_chunk = g.tiles_per_chunk;
-    p.nsteps = nsteps;
+    p.nsteps = 1;
     p.lookahead = g.lookahead;
-    cudaError_t e = cudaMemsetAsync(s.sync, 0, (2 + 2 * (size_t)g.nchunks) * sizeof(unsigned), s.stream);
-    if (e != cudaSuccess) return e;
-    ELBM_DISPATCH_STORAGE(s.storage, { k_pipelined<D, ST><<<g.grid, kBlock, 0, s.stream>>>(p); });
-    ++*launches;
+    for (int k = 0; k < nsteps; ++k) {
+        p.parity = (parity + k) & 1;
+        cudaError_t e = cudaMemsetAsync(s.sync, 0, (2 + 2 * (size_t)g.nchunks) * sizeof(unsigned), s.stream);
+        if (e != cudaSuccess) return e;
+        ELBM_DISPATCH_STORAGE(s.storage, {
+            if (p.parity == 0) k_pipelined<D, ST, 0><<<g.grid, kBlock, 0, s.stream>>>(p);
+            else k_pipelined<D, ST, 1><<<g.grid, kBlock, 0, s.stream>>>(p);
+        });
+        ++*launches;
+    }
     return cudaGetLastError();
 }
 

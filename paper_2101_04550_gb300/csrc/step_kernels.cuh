@@ -98,15 +98,13 @@ __global__ void __launch_bounds__(kBlock) k_init(StepParams p, const TIn* rho, c
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
     const float drho = (float)((double)rho[cell] - (double)p.rho_ref);
-    float uu[3], dP[3];
+    float uu[3], zero[3] = {0.f, 0.f, 0.f}, du[3], dP[3];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        uu[a] = (float)u[(size_t)a * p.N + cell];
-        dP[a] = uu[a] * uu[a];
-    }
+    for (int a = 0; a < D; ++a) uu[a] = (float)u[(size_t)a * p.N + cell];
+    baseline_args<D>(p, uu, zero, du, dP);
     typename S::T* f = static_cast<typename S::T*>(p.f);
-    for_each_equilibrium<D>(p, drho, uu, dP, [&](int i, float geq) {
-        S::store(f + i * p.N + cell, S::shifted ? geq : geq + p.w[i] * p.rho_ref);
+    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
+        S::store(f + i * p.N + cell, S::shifted ? geq : geq + p.bw[i] * p.rho_ref);
     });
 }
 
@@ -127,39 +125,32 @@ cudaError_t init_impl(const Solver& s, const void* rho, const void* u, int dtype
 }
 
 // ------------------------------------------------------------- read-outs
-// Post-streaming population i of a node, as a deviation g_i, at the solver's
+// Post-streaming populations of a node as deviations g_i, at the solver's
 // current parity (not a hot path: parity is a run-time value here).
 template <int D, int ST>
-__device__ __forceinline__ double load_dev(const StepParams& p, const Node& n, int i)
+__device__ __forceinline__ void gather_any(const StepParams& p, const Node& n, float* g)
 {
-    using S = Storage<ST>;
-    const typename S::T* f = static_cast<const typename S::T*>(p.f);
-    const float v = S::load(f + read_slot<D>(n, p.N, i, p.parity));
-    return S::shifted ? (double)v : (double)v - (double)p.w[i] * (double)p.rho_ref;
+    if (p.parity == 0) gather<D, ST, 0>(p, n, g);
+    else gather<D, ST, 1>(p, n, g);
 }
 
-// rho and u of every node (Eqs. density, momentum), summed in FP64;
-// with a body force u is reported at the half step, u + g/2.
+// rho and u of every node (Eqs. density, momentum) with the step kernels'
+// FP32 sums; with a body force u is reported at the half step, u + g/2.
 template <int D, int ST, typename TOut>
 __global__ void __launch_bounds__(kBlock) k_moments(StepParams p, TOut* rho, TOut* u)
 {
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
     const Node n = make_node<D>(p, cell);
-    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-    for (int i = 0; i < Lat<D>::Q; ++i) {
-        const double v = load_dev<D, ST>(p, n, i);
-        r += v;
-        jx += cx_of(i) * v;
-        jy += cy_of(i) * v;
-        jz += cz_of<D>(i) * v;
-    }
-    r += (double)p.rho_ref;
+    float g[Lat<D>::Q];
+    gather_any<D, ST>(p, n, g);
+    float drho, j[3];
+    moments<D>(p, g, drho, j);
+    const float r = p.rho_ref + drho;
+    const float inv_r = 1.0f / r;
     rho[cell] = (TOut)r;
-    const double j[3] = {jx * p.lam[0], jy * p.lam[1], jz * p.lam[2]};
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[(size_t)a * p.N + cell] = (TOut)(j[a] / r + 0.5 * (double)p.g[a]);
+    for (int a = 0; a < D; ++a) u[(size_t)a * p.N + cell] = (TOut)(j[a] * inv_r + 0.5f * p.g[a]);
 }
 
 template <int D>
@@ -178,6 +169,16 @@ cudaError_t moments_impl(const Solver& s, void* rho, void* u, int dtype, long lo
     return cudaGetLastError();
 }
 
+// Post-streaming population i of a node, unshifted, in FP64.
+template <int D, int ST>
+__device__ __forceinline__ double load_f64(const StepParams& p, const Node& n, int i)
+{
+    using S = Storage<ST>;
+    const typename S::T* f = static_cast<const typename S::T*>(p.f);
+    const float v = S::load(f + read_slot<D>(n, p.N, i, p.parity));
+    return S::shifted ? (double)v + (double)p.bw[i] * (double)p.rho_ref : (double)v;
+}
+
 // Unshifted post-streaming populations f_i = g_i + w_i rho_ref, layout f[i][cell].
 template <int D, int ST, typename TOut>
 __global__ void __launch_bounds__(kBlock) k_get_f(StepParams p, TOut* out)
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) k_get_f(StepParams p, TOut* out)
     const Node n = make_node<D>(p, cell);
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i)
-        out[(size_t)i * p.N + cell] = (TOut)(load_dev<D, ST>(p, n, i) + (double)p.w[i] * (double)p.rho_ref);
+        out[(size_t)i * p.N + cell] = (TOut)load_f64<D, ST>(p, n, i);
 }
 
 // Store caller populations at the even-parity slots.
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kBlock) k_set_f(StepParams p, const TIn* in)
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
         const double v = (double)in[(size_t)i * p.N + cell];
-        const double stored = S::shifted ? v - (double)p.w[i] * (double)p.rho_ref : v;
+        const double stored = S::shifted ? v - (double)p.bw[i] * (double)p.rho_ref : v;
         S::store(f + i * p.N + cell, (float)stored);
     }
 }
@@ -235,29 +236,28 @@ cudaError_t set_populations_impl(const Solver& s, const void* f, int dtype, long
 }
 
 // ------------------------------------------------------- FP64 diagnostics
-// Stage 1: per node rho, u (FP32) and min_i f_i into scratch mom[5][N].
+// Stage 1: per node rho, u and min_i f_i (FP32, the step kernels' sums) into
+// scratch mom[5][N].
 template <int D, int ST>
 __global__ void __launch_bounds__(kBlock) k_red_nodes(StepParams p, float* mom)
 {
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
     const Node n = make_node<D>(p, cell);
-    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, fmin = DBL_MAX;
+    float g[Lat<D>::Q];
+    gather_any<D, ST>(p, n, g);
+    float drho, j[3];
+    moments<D>(p, g, drho, j);
+    float fmin = FLT_MAX;
 #pragma unroll
-    for (int i = 0; i < Lat<D>::Q; ++i) {
-        const double v = load_dev<D, ST>(p, n, i);
-        r += v;
-        jx += cx_of(i) * v;
-        jy += cy_of(i) * v;
-        jz += cz_of<D>(i) * v;
-        fmin = fmin < v + (double)p.w[i] * p.rho_ref ? fmin : v + (double)p.w[i] * p.rho_ref;
-    }
-    r += (double)p.rho_ref;
-    mom[cell] = (float)r;
-    mom[(size_t)p.N + cell] = (float)(jx * p.lam[0] / r + 0.5 * (double)p.g[0]);
-    mom[(size_t)2 * p.N + cell] = (float)(jy * p.lam[1] / r + 0.5 * (double)p.g[1]);
-    mom[(size_t)3 * p.N + cell] = (D == 3) ? (float)(jz * p.lam[2] / r + 0.5 * (double)p.g[2]) : 0.f;
-    mom[(size_t)4 * p.N + cell] = (float)fmin;
+    for (int i = 0; i < Lat<D>::Q; ++i) fmin = fminf(fmin, fmaf(p.bw[i], p.rho_ref, g[i]));
+    const float r = p.rho_ref + drho;
+    const float inv_r = 1.0f / r;
+    mom[cell] = r;
+    mom[(size_t)p.N + cell] = j[0] * inv_r + 0.5f * p.g[0];
+    mom[(size_t)2 * p.N + cell] = j[1] * inv_r + 0.5f * p.g[1];
+    mom[(size_t)3 * p.N + cell] = (D == 3) ? j[2] * inv_r + 0.5f * p.g[2] : 0.f;
+    mom[(size_t)4 * p.N + cell] = fmin;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -313,36 +313,36 @@ __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* m
     const float* ux = mom + p.N;
     const float* uy = mom + 2 * (size_t)p.N;
     const float* uz = mom + 3 * (size_t)p.N;
+    const float ix = 0.5f / p.lam[0], iy = 0.5f / p.lam[1], iz = 0.5f / p.lam[2];
     for (int cell = blockIdx.x * kBlock + threadIdx.x; cell < p.N; cell += gridDim.x * kBlock) {
         const Node n = make_node<D>(p, cell);
-        const double r = mom[cell];
-        const double u0 = ux[cell], u1 = uy[cell], u2 = uz[cell];
-        const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+        const float r = mom[cell];
+        const float u0 = ux[cell], u1 = uy[cell], u2 = uz[cell];
+        const float uu = u0 * u0 + u1 * u1 + u2 * u2;
         const bool finite = isfinite(r) && isfinite(uu);
-        acc[0] += r;
-        acc[1] += r * u0;
-        acc[2] += r * u1;
-        acc[3] += r * u2;
-        acc[4] += r * uu;
-        acc[5] += uu;
-        const double ix = 0.5 / p.lam[0], iy = 0.5 / p.lam[1], iz = 0.5 / p.lam[2];
-        const double dxuy = ((double)uy[n.at(1, 0, 0)] - uy[n.at(-1, 0, 0)]) * ix;
-        const double dyux = ((double)ux[n.at(0, 1, 0)] - ux[n.at(0, -1, 0)]) * iy;
-        double w2 = (dxuy - dyux) * (dxuy - dyux);
+        const float dxuy = (uy[n.at(1, 0, 0)] - uy[n.at(-1, 0, 0)]) * ix;
+        const float dyux = (ux[n.at(0, 1, 0)] - ux[n.at(0, -1, 0)]) * iy;
+        float w2 = (dxuy - dyux) * (dxuy - dyux);
         if (D == 3) {
-            const double dyuz = ((double)uz[n.at(0, 1, 0)] - uz[n.at(0, -1, 0)]) * iy;
-            const double dzuy = ((double)uy[n.at(0, 0, 1)] - uy[n.at(0, 0, -1)]) * iz;
-            const double dzux = ((double)ux[n.at(0, 0, 1)] - ux[n.at(0, 0, -1)]) * iz;
-            const double dxuz = ((double)uz[n.at(1, 0, 0)] - uz[n.at(-1, 0, 0)]) * ix;
+            const float dyuz = (uz[n.at(0, 1, 0)] - uz[n.at(0, -1, 0)]) * iy;
+            const float dzuy = (uy[n.at(0, 0, 1)] - uy[n.at(0, 0, -1)]) * iz;
+            const float dzux = (ux[n.at(0, 0, 1)] - ux[n.at(0, 0, -1)]) * iz;
+            const float dxuz = (uz[n.at(1, 0, 0)] - uz[n.at(-1, 0, 0)]) * ix;
             w2 += (dyuz - dzuy) * (dyuz - dzuy) + (dzux - dxuz) * (dzux - dxuz);
         }
-        acc[6] += w2;
-        const double dxux = ((double)ux[n.at(1, 0, 0)] - ux[n.at(-1, 0, 0)]) * ix;
-        acc[7] += dxux * dxux;
-        acc[8] += u0 * u0;
+        const float dxux = (ux[n.at(1, 0, 0)] - ux[n.at(-1, 0, 0)]) * ix;
+        acc[0] += (double)r;
+        acc[1] += (double)(r * u0);
+        acc[2] += (double)(r * u1);
+        acc[3] += (double)(r * u2);
+        acc[4] += (double)(r * uu);
+        acc[5] += (double)uu;
+        acc[6] += (double)w2;
+        acc[7] += (double)(dxux * dxux);
+        acc[8] += (double)(u0 * u0);
         acc[9] = fmin(acc[9], (double)mom[4 * (size_t)p.N + cell]);
         acc[10] += finite ? 0.0 : 1.0;
-        acc[11] = fmax(acc[11], finite ? sqrt(uu) : 0.0);
+        acc[11] = fmax(acc[11], finite ? (double)sqrtf(uu) : 0.0);
     }
     block_reduce(acc, partials + (size_t)blockIdx.x * ELBM_NRED);
 }
@@ -362,6 +362,38 @@ __global__ void __launch_bounds__(kBlock) k_red_final(const double* partials, in
             acc[k] = (k == 9) ? fmin(acc[k], q[k]) : (k == 11) ? fmax(acc[k], q[k]) : acc[k] + q[k];
     }
     block_reduce(acc, out);
+}
+
+// Sums of rho and rho u_a of a caller field (FP64), for the automatic storage
+// baseline velocity: out[0] = sum rho, out[1 + a] = sum rho u_a.
+template <int D, typename TIn>
+__global__ void __launch_bounds__(kBlock) k_field_sums(int N, const TIn* rho, const TIn* u, double* partials)
+{
+    double acc[ELBM_NRED];
+#pragma unroll
+    for (int k = 0; k < ELBM_NRED; ++k) acc[k] = 0.0;
+    acc[9] = DBL_MAX;
+    for (int cell = blockIdx.x * kBlock + threadIdx.x; cell < N; cell += gridDim.x * kBlock) {
+        const double r = (double)rho[cell];
+        acc[0] += r;
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[1 + a] += r * (double)u[(size_t)a * N + cell];
+    }
+    block_reduce(acc, partials + (size_t)blockIdx.x * ELBM_NRED);
+}
+
+template <int D>
+cudaError_t field_sums_impl(const Solver& s, const void* rho, const void* u, int dtype, long long* launches)
+{
+    if (dtype == ELBM_DTYPE_F64)
+        k_field_sums<D, double><<<s.red_blocks, kBlock, 0, s.stream>>>((int)s.N, (const double*)rho,
+                                                                      (const double*)u, s.partials);
+    else
+        k_field_sums<D, float><<<s.red_blocks, kBlock, 0, s.stream>>>((int)s.N, (const float*)rho,
+                                                                     (const float*)u, s.partials);
+    k_red_final<D><<<1, kBlock, 0, s.stream>>>(s.partials, s.red_blocks, s.red_out);
+    *launches += 2;
+    return cudaGetLastError();
 }
 
 template <int D>

@@ -20,6 +20,7 @@ F32, F16_SHIFT, BF16_SHIFT, F32_SHIFT = 0, 1, 2, 3
 DTYPE_F32, DTYPE_F64 = 0, 1
 OPT_EQUILIBRIUM, OPT_KERNEL, OPT_RHO_REF = 1, 2, 3
 OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z, OPT_WALLS_Y = 4, 5, 6, 7
+OPT_U_REF_X, OPT_U_REF_Y, OPT_U_REF_Z, OPT_U_REF_AUTO = 8, 9, 10, 11
 NRED = 12
 ERRORS = {0: "OK", -1: "ARG", -2: "UNREALIZABLE", -3: "OOM", -4: "CUDA", -5: "NONFINITE",
           -6: "TIMEOUT", -7: "STATE"}
@@ -32,7 +33,8 @@ _lock = threading.Lock()
 _lib = None
 EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_step", "elbm_moments",
            "elbm_get_populations", "elbm_set_populations", "elbm_reduce", "elbm_sync", "elbm_cells",
-           "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_last_error"]
+           "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
+           "elbm_last_error"]
 
 
 class ElbmError(RuntimeError):
@@ -74,6 +76,7 @@ def load(build_if_missing: bool = True):
             getattr(L, name).restype = ctypes.c_longlong
         L.elbm_omega.argtypes = [vp]
         L.elbm_omega.restype = dp
+        L.elbm_get_u_ref.argtypes = [vp, ctypes.POINTER(dp)]
         L.elbm_last_error.argtypes = []
         L.elbm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -108,7 +111,7 @@ class Solver:
     """One periodic grid on the GPU, advanced by the extended LBGK step."""
 
     def __init__(self, lattice, n, stretch=(1.0, 1.0, 1.0), T=1.0 / 3.0, nu=0.01, storage=F32,
-                 stream=None, kernel=0, equilibrium=0):
+                 stream=None, kernel=0, equilibrium=0, u_ref=None):
         L = load()
         self.lattice = lattice
         self.D = 2 if lattice == D2Q9 else 3
@@ -139,6 +142,11 @@ class Solver:
             self.set_option(OPT_KERNEL, kernel)
         if equilibrium:
             self.set_option(OPT_EQUILIBRIUM, equilibrium)
+        if isinstance(u_ref, str) and u_ref == "mean":
+            self.set_option(OPT_U_REF_AUTO, 1)
+        elif u_ref is not None:
+            for a, v in enumerate(u_ref):
+                self.set_option(OPT_U_REF_X + a, float(v))
 
     # -- lifetime -------------------------------------------------------
     def close(self):
@@ -209,6 +217,12 @@ class Solver:
         if rc != 0 and not (rc == -5 and not raise_nonfinite):
             _check(rc)
         return vals
+
+    @property
+    def u_ref(self):
+        out = (ctypes.c_double * 3)()
+        _check(load().elbm_get_u_ref(self._h, out))
+        return tuple(out)[: self.D]
 
     @property
     def omega(self):

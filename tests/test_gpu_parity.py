@@ -23,9 +23,9 @@ def rel_linf(a, b):
 
 
 def run_gpu(lattice, n, lam, T, nu, rho, u, steps, storage=elbm.F32, kernel=1, equilibrium=0,
-            chunked=None):
+            chunked=None, u_ref=None):
     with elbm.Solver(lattice, n, stretch=lam, T=T, nu=nu, storage=storage, kernel=kernel,
-                     equilibrium=equilibrium) as s:
+                     equilibrium=equilibrium, u_ref=u_ref) as s:
         s.init(rho, u)
         if chunked:
             for k in chunked:
@@ -96,11 +96,35 @@ def test_d2q9_product_form_mode():
 
 
 @pytest.mark.parametrize("storage", [elbm.F16_SHIFT, elbm.BF16_SHIFT])
-def test_d2q9_half_storage(storage):
+def test_d2q9_half_storage_advected(storage):
+    """Half-precision storage of an advected rotated wave (U = 0.1, amplitude
+    1e-2), with the storage baseline at the field's mean velocity."""
     n = (64, 64)
     rho, u, _, _ = inputs.shear_wave(n, (1.0, 1.0), (1, 1), (-1, 1), 1e-2, 0.1)
-    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, 1)
+    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, 1, u_ref="mean")
     _, uo = run_oracle(2, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000)
+    assert rel_linf(ug, uo) <= TOL[storage]
+
+
+def test_baseline_velocity_mean_is_detected_and_harmless_in_fp32():
+    n = (64, 64)
+    rho, u, _, _ = inputs.shear_wave(n, (1.0, 1.0), (1, 1), (-1, 1), 1e-2, 0.1)
+    with elbm.Solver(elbm.D2Q9, n, T=1 / 3, nu=0.01, storage=elbm.F32_SHIFT, u_ref="mean") as s:
+        s.init(rho, u)
+        np.testing.assert_allclose(s.u_ref, [0.1 / np.sqrt(2)] * 2, rtol=1e-6)
+        s.step(1000)
+        _, ug = s.moments()
+    _, uo = run_oracle(2, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", [elbm.F16_SHIFT, elbm.BF16_SHIFT])
+def test_d3q27_half_storage_turbulence(storage):
+    """Zero-mean turbulence (rest baseline, f_i - w_i rho0): 48^3, u_rms = 0.08, 200 steps."""
+    n = (48, 48, 48)
+    rho, u = inputs.isotropic_turbulence(n, seed=6, k0=4.0, u_rms=0.08)
+    _, ug = run_gpu(elbm.D3Q27, n, (1.0, 1.0, 1.0), 0.5, 0.02, rho, u, 200, storage, 2)
+    _, uo = run_oracle(3, n, (1.0, 1.0, 1.0), 0.5, 0.02, rho, u, 200)
     assert rel_linf(ug, uo) <= TOL[storage]
 
 
