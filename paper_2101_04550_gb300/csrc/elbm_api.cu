@@ -41,22 +41,6 @@ size_t storage_bytes(int storage)
     return (storage == ELBM_F16_SHIFT || storage == ELBM_BF16_SHIFT) ? 2 : 4;
 }
 
-// Rest triplet per axis, Psi_c(0, T, lam) = (T/(2 lam^2), 1 - T/lam^2, T/(2 lam^2))
-// (Eqs. phi0S, phiPlusS, phiMinusS at u = 0, P = T).  The centre value is
-// rounded to a multiple of 2^-24 and the side values are (1 - centre)/2, so
-// that the three floats sum to exactly one: the equilibrium then carries
-// exactly rho and rho u in every product (a sum of 1 + eps would scale the
-// momentum by 1 + eps each step).  The implied temperature differs from T by
-// at most 2^-24 lam^2.
-static void rest_triplet(double T, double lam, float out[3])
-{
-    const double centre = std::nearbyint((1.0 - T / (lam * lam)) * 16777216.0) / 16777216.0;
-    const double side = 0.5 * (1.0 - centre);
-    out[0] = (float)side;
-    out[2] = (float)side;
-    out[1] = (float)centre;
-}
-
 // Storage-baseline triplet per axis, Psi_c(U0, T + U0^2, lam), rounded so that
 // the three floats sum to exactly one (centre a multiple of 2^-24, sides
 // multiples of 2^-25).  Returns false if a value is not positive.  *u0_eff
@@ -77,6 +61,17 @@ bool base_triplet(double T, double lam, double U0, float out[3], double* u0_eff)
 
 static bool shifted_storage(int storage) { return storage != ELBM_F32; }
 
+// Round-up multiplier and shift for floor(n / d), 0 <= n < 2^31, d >= 1:
+// t = umulhi(n, m), q = (t + n) >> s with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1.
+static void host_divider(unsigned d, unsigned* m, int* s)
+{
+    int k = 0;
+    while ((1ull << k) < d) ++k;
+    *s = k;
+    *m = (unsigned)(((1ull << 32) * ((1ull << k) - d)) / d + 1);
+}
+
 void fill_params(const Solver& s, StepParams& p)
 {
     std::memset(&p, 0, sizeof p);
@@ -89,6 +84,8 @@ void fill_params(const Solver& s, StepParams& p)
     p.nz = s.nz;
     p.N = (int)s.N;
     p.plane = s.nx * s.ny;
+    host_divider((unsigned)s.nx, &p.div_nx_m, &p.div_nx_s);
+    host_divider((unsigned)p.plane, &p.div_plane_m, &p.div_plane_s);
     for (int a = 0; a < 3; ++a) {
         const double l = s.lam[a];
         p.lam[a] = (float)l;
@@ -96,8 +93,6 @@ void fill_params(const Solver& s, StepParams& p)
         p.inv_lam2[a] = (float)(1.0 / (l * l));
         p.inv_2lam[a] = (float)(0.5 / l);
         p.lam2m3T[a] = (float)(l * l - 3.0 * s.T);
-        rest_triplet(s.T, l, p.rest[a]);
-        p.inv_theta[a] = (float)(1.0 / (2.0 * (double)p.rest[a][0]));
     }
     for (int a = 0; a < 3; ++a) {
         const double U0 = (a < s.D && shifted_storage(s.storage)) ? s.u_ref[a] : 0.0;
@@ -108,13 +103,14 @@ void fill_params(const Solver& s, StepParams& p)
     }
     for (int i = 0; i < s.Q; ++i) {
         const int c[3] = {i % 3, (i / 3) % 3, i / 9};
-        double w = 1.0, b = 1.0;
-        for (int a = 0; a < s.D; ++a) {
-            w *= (double)p.rest[a][c[a]];
-            b *= (double)p.base[a][c[a]];
-        }
-        p.w[i] = (float)w;
+        double b = 1.0;
+        for (int a = 0; a < s.D; ++a) b *= (double)p.base[a][c[a]];
         p.bw[i] = (float)b;
+    }
+    for (int cx = 0; cx < 3; ++cx) {
+        p.base_xr[cx] = (float)(s.rho_ref * (double)p.base[0][cx]);
+        for (int cy = 0; cy < 3; ++cy)
+            p.bxy_r[cx + 3 * cy] = (float)(s.rho_ref * (double)p.base[0][cx] * (double)p.base[1][cy]);
     }
     p.T = (float)s.T;
     p.omega = (float)s.omega;

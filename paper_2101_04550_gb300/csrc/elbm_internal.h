@@ -22,15 +22,16 @@ struct StepParams {
     int nx, ny, nz;       // nodes per axis (nz = 1 for D2Q9)
     int N;                // nx*ny*nz
     int plane;            // nx*ny
+    unsigned div_nx_m, div_plane_m;  // round-up multipliers for division by nx and by nx*ny
+    int div_nx_s, div_plane_s;       // and their shifts
     float lam[3];         // stretching factors lam_a
     float inv_lam[3];     // 1/lam_a
     float inv_lam2[3];    // 1/lam_a^2
     float inv_2lam[3];    // 1/(2 lam_a): central-difference weight (node spacing lam_a)
     float lam2m3T[3];     // lam_a^2 - 3T
-    float rest[3][3];     // rest triplet per axis: Psi_c(0, T, lam_a), index c+1
-    float w[kMaxQ];       // rest weights w_i = prod_a rest[a][c_ia+1] (conservation projection)
-    float inv_theta[3];   // 1 / sum_i w_i c_ia^2 = 1 / (2 rest[a][0])
     float base[3][3];     // storage baseline triplet per axis: Psi_c(U0_a, T + U0_a^2, lam_a)
+    float base_xr[3];     // rho_ref base[0][c]
+    float bxy_r[9];       // rho_ref base[0][cx] base[1][cy], index cx + 3 cy
     float bw[kMaxQ];      // storage baseline b_i = prod_a base[a][c_ia+1]; stored g_i = f_i - rho_ref b_i
     float u0[3];          // baseline velocity U0 (zero unless set)
     float j0[3];          // rho_ref U0: baseline momentum

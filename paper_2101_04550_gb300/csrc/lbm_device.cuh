@@ -2,10 +2,11 @@
 // storage conversion, AA-pattern gather/scatter, moments, the diagonal anomaly
 // and the product-form extended equilibrium with BGK relaxation.
 //
-// Arithmetic is FP32.  Populations are handled as deviations from the rest
-// equilibrium, g_i = f_i - w_i rho_ref with w_i = Psi_i(0, T, lam), so that the
-// large constant part never enters a rounding step; the equilibrium deviation
-// rho Psi_i - rho_ref w_i is formed from per-axis differences (see relax()).
+// Arithmetic is FP32.  Populations are handled as deviations from a baseline
+// equilibrium, g_i = f_i - rho_ref b_i with b_i = Psi_i(U0, T + U0^2, lam) (the
+// rest weights w_i for U0 = 0), so that the large constant part never enters
+// a rounding step; the equilibrium deviation rho Psi_i - rho_ref b_i is formed
+// from per-axis differences (see for_each_equilibrium()).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -71,14 +72,21 @@ struct Node {
     __device__ int at(int cx, int cy, int cz) const { return ox[cx + 1] + oy[cy + 1] + oz[cz + 1]; }
 };
 
+// floor(n / d) for 0 <= n < 2^31 with the round-up multiplier of d
+// (m, s from host_divider): t = umulhi(n, m), q = (t + n) >> s.
+__device__ __forceinline__ int fast_div(int n, unsigned m, int s)
+{
+    return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> s);
+}
+
 template <int D>
 __device__ __forceinline__ Node make_node(const StepParams& p, int cell)
 {
     Node n;
     n.cell = cell;
-    const int z = cell / p.plane;
+    const int z = (D == 3) ? fast_div(cell, p.div_plane_m, p.div_plane_s) : 0;
     const int r = cell - z * p.plane;
-    const int y = r / p.nx;
+    const int y = fast_div(r, p.div_nx_m, p.div_nx_s);
     const int x = r - y * p.nx;
     n.ox[1] = x;
     n.ox[0] = (x == 0) ? p.nx - 1 : x - 1;
@@ -197,21 +205,25 @@ __device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float 
 #pragma unroll
         for (int c = 0; c < 3; ++c) A[a][c] = p.base[a][c] + dl[a][c];
     }
+    // rho_ref is folded into the x factors: dlx_r = rho_ref delta_x, base_xr = rho_ref base_x
+    float dlx_r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dlx_r[c] = p.rho_ref * dl[0][c];
 #pragma unroll
     for (int cy = 0; cy < 3; ++cy) {
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
             const float pxy = A[0][cx] * A[1][cy];
-            const float dxy = fmaf(dl[0][cx], A[1][cy], p.base[0][cx] * dl[1][cy]);
+            // rho_ref (prod_{x,y} Psi - prod_{x,y} base)
+            const float dxy_r = fmaf(dlx_r[cx], A[1][cy], p.base_xr[cx] * dl[1][cy]);
             if (D == 2) {
-                fn(cx + 3 * cy, fmaf(drho, pxy, p.rho_ref * dxy));
+                fn(cx + 3 * cy, fmaf(drho, pxy, dxy_r));
             } else {
-                const float bxy = p.base[0][cx] * p.base[1][cy];
 #pragma unroll
                 for (int cz = 0; cz < 3; ++cz) {
                     const float psi = pxy * A[2][cz];
-                    const float dpsi = fmaf(dxy, A[2][cz], bxy * dl[2][cz]);
-                    fn(cx + 3 * cy + 9 * cz, fmaf(drho, psi, p.rho_ref * dpsi));
+                    const float dpsi_r = fmaf(dxy_r, A[2][cz], p.bxy_r[cx + 3 * cy] * dl[2][cz]);
+                    fn(cx + 3 * cy + 9 * cz, fmaf(drho, psi, dpsi_r));
                 }
             }
         }
@@ -231,6 +243,16 @@ __device__ __forceinline__ void baseline_args(const StepParams& p, const float* 
     }
 }
 
+// Slot of population i among the ones that carry the conservation
+// correction (rest, then -x, +x, -y, +y, -z, +z), or -1.
+template <int D>
+__host__ __device__ constexpr int corrected_slot(int i)
+{
+    constexpr int I0 = (Lat<D>::Q - 1) / 2;
+    return i == I0 ? 0 : i == I0 - 1 ? 1 : i == I0 + 1 ? 2 : i == I0 - 3 ? 3 : i == I0 + 3 ? 4
+         : (D == 3 && i == I0 - 9) ? 5 : (D == 3 && i == I0 + 9) ? 6 : -1;
+}
+
 // Relax g toward the extended equilibrium (Eq. LBGK with f* of Eq. 27eqext).
 // d[a] is the central difference of the anomaly along axis a; the pressure
 // diagonal is P*_aa = T + u_a^2 + (2-omega)/(2 rho omega) d_a (Eq. Paastar1).
@@ -239,15 +261,16 @@ __device__ __forceinline__ void baseline_args(const StepParams& p, const float* 
 // momentum), so relaxation conserves them.  In FP32 the rounding of rho, of
 // u = j/rho and of the triplet terms leaves the computed equilibrium with a
 // mass and momentum off by a fraction of an ulp, and in near-uniform flow
-// that error has the same sign at every node and every step.  So the
-// increments dlt_i = geq_i - g_i (small numbers, summed accurately) have their
-// zeroth and first moments e0, e_a projected out along the rest weights,
-//   dlt_i -= w_i (e0 + sum_a c_ia e_a / theta_a),  theta_a = sum_i w_i c_ia^2,
-// before the single rounding of g + omega dlt.
+// that error has the same sign at every node and every step.  So the moments
+// e0 = sum_i dlt_i and e_a = sum_i c_ia dlt_i of the increments
+// dlt_i = geq_i - g_i (small numbers, summed accurately) are removed before
+// the single rounding of g + omega dlt: e0 from the rest population and
+// +-e_a/2 from the two populations along axis a.
 template <int D>
 __device__ __forceinline__ void relax(const StepParams& p, float* g, float drho, const float* j,
                                       const float* d)
 {
+    constexpr int I0 = (Lat<D>::Q - 1) / 2;
     const float rho = p.rho_ref + drho;
     const float inv_rho = 1.0f / rho;
     float u[3], pcorr[3], du[3], dP[3];
@@ -257,9 +280,9 @@ __device__ __forceinline__ void relax(const StepParams& p, float* g, float drho,
         pcorr[a] = p.coef * inv_rho * d[a];
     }
     baseline_args<D>(p, u, pcorr, du, dP);
-    // pass 1: moments of the increments (the equilibrium is recomputed in
-    // pass 2 instead of being kept, which saves Q registers per thread)
+    const float om = p.omega;
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    float keep[2 * D + 1];
     for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
         const float dl = geq - g[i];
         e0 += dl;
@@ -269,14 +292,21 @@ __device__ __forceinline__ void relax(const StepParams& p, float* g, float drho,
         if (cy_of(i) == -1) ey -= dl;
         if (cz_of<D>(i) == 1) ez += dl;
         if (cz_of<D>(i) == -1) ez -= dl;
+        const int k = corrected_slot<D>(i);
+        if (k >= 0) keep[k] = geq;
+        else g[i] = fmaf(om, dl, g[i]);
     });
-    const float kx = ex * p.inv_theta[0], ky = ey * p.inv_theta[1], kz = (D == 3) ? ez * p.inv_theta[2] : 0.f;
-    const float om = p.omega;
-    // pass 2: projected relaxation, one rounding per population
-    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
-        const float proj = p.w[i] * (e0 + cx_of(i) * kx + cy_of(i) * ky + cz_of<D>(i) * kz);
-        g[i] = fmaf(om, (geq - g[i]) - proj, g[i]);
-    });
+    const float hx = 0.5f * ex, hy = 0.5f * ey;
+    g[I0] = fmaf(om, (keep[0] - g[I0]) - e0, g[I0]);
+    g[I0 - 1] = fmaf(om, (keep[1] - g[I0 - 1]) + hx, g[I0 - 1]);
+    g[I0 + 1] = fmaf(om, (keep[2] - g[I0 + 1]) - hx, g[I0 + 1]);
+    g[I0 - 3] = fmaf(om, (keep[3] - g[I0 - 3]) + hy, g[I0 - 3]);
+    g[I0 + 3] = fmaf(om, (keep[4] - g[I0 + 3]) - hy, g[I0 + 3]);
+    if (D == 3) {
+        const float hz = 0.5f * ez;
+        g[I0 - 9] = fmaf(om, (keep[5] - g[I0 - 9]) + hz, g[I0 - 9]);
+        g[I0 + 9] = fmaf(om, (keep[6] - g[I0 + 9]) - hz, g[I0 + 9]);
+    }
 }
 
 }  // namespace elbm

@@ -36,7 +36,11 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 // Resident blocks per SM the pipelined kernel is compiled for (register cap
 // 65536 / (256 * ELBM_PIPE_MIN_BLOCKS)).
 #ifndef ELBM_PIPE_MIN_BLOCKS
-#define ELBM_PIPE_MIN_BLOCKS 3
+#define ELBM_PIPE_MIN_BLOCKS 2
+#endif
+// Nodes per thread in one tile of the pipelined kernel.
+#ifndef ELBM_PIPE_TILE_CPT
+#define ELBM_PIPE_TILE_CPT 4
 #endif
 
 // Layout of the sync words (the first 2 + 2K are reset by the host before
@@ -60,21 +64,36 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Bounded wait until *ctr >= target.  False if it gave up (timeout or abort).
-__device__ __forceinline__ bool wait_ge(const StepParams& p, const unsigned* ctr, unsigned target)
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p)
 {
-    if (ld_acquire(ctr) >= target) return true;
-    const unsigned long long t0 = globaltimer();
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Bounded wait until the three counters a, b, c are all >= target; the three
+// loads are issued together and one fence then orders the block's later reads
+// after the producers' releases.  False if it gave up (timeout or abort).
+__device__ __forceinline__ bool wait3_ge(const StepParams& p, const unsigned* a, const unsigned* b,
+                                         const unsigned* c, unsigned target)
+{
+    unsigned long long t0 = 0;
     volatile unsigned* abort_flag = p.sync + 1;
-    while (true) {
-        __nanosleep(32);
-        if (ld_acquire(ctr) >= target) return true;
-        if (*abort_flag) return false;
+    for (int it = 0;; ++it) {
+        const unsigned va = ld_relaxed(a), vb = ld_relaxed(b), vc = ld_relaxed(c);
+        if (va >= target && vb >= target && vc >= target) {
+            fence_acquire();
+            return true;
+        }
+        if (it == 0) t0 = globaltimer();
+        else if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitLimitNs) {
             atomicExch(p.sync + 1, 1u);
             atomicCAS(p.status, 0, ELBM_ERR_TIMEOUT);
             return false;
         }
+        __nanosleep(32);
     }
 }
 
@@ -109,8 +128,7 @@ __global__ void __launch_bounds__(kBlock, ELBM_PIPE_MIN_BLOCKS) k_pipelined(Step
             bool ok = true;
             if (type == 1) {
                 const int cm = (c == 0) ? K - 1 : c - 1, cp = (c == K - 1) ? 0 : c + 1;
-                const unsigned tgt = (unsigned)T;
-                ok = wait_ge(p, done_a + cm, tgt) && wait_ge(p, done_a + c, tgt) && wait_ge(p, done_a + cp, tgt);
+                ok = wait3_ge(p, done_a + cm, done_a + c, done_a + cp, (unsigned)T);
             }
             s_ok = ok;
         }
@@ -172,7 +190,7 @@ PipeGeom pipelined_geometry_impl(const Solver& s)
     g.grid = pipelined_grid_impl<D>(s);
     g.chunk_planes = std::max(1, std::min(nlayers, (65536 + layer - 1) / layer));
     g.nchunks = (nlayers + g.chunk_planes - 1) / g.chunk_planes;
-    g.tile_cells = 2 * kBlock;
+    g.tile_cells = ELBM_PIPE_TILE_CPT * kBlock;
     const int chunk_cells = g.chunk_planes * layer;
     g.tiles_per_chunk = (chunk_cells + g.tile_cells - 1) / g.tile_cells;
     const int L = (g.grid + 2 * g.tiles_per_chunk - 1) / (2 * g.tiles_per_chunk) + 1;
