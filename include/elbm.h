@@ -71,9 +71,9 @@ extern "C" {
  *   2 = product form truncated to second order in u (Sec. III preamble). */
 #define ELBM_OPT_EQUILIBRIUM 1
 /* ELBM_OPT_KERNEL: 0 = automatic; 1 = two-pass (anomaly pass, collide pass);
- *   2 = pipelined pass (same arithmetic; one launch per step whose tiles are
- *   handed out by an atomic ticket so that the collide phase re-reads the
- *   populations from L2). */
+ *   2 = pipelined pass (same arithmetic; one cooperative launch per step whose
+ *   warps interleave the two phases chunk by chunk, so that the collide phase
+ *   re-reads the populations from L2). */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3

@@ -176,6 +176,35 @@ bool pipelined_usable(const elbm_solver* s) { return s->pipe.grid > 0 && s->sync
 
 bool shifted_storage_mode(int storage) { return storage != ELBM_F32; }
 
+// Kernel form a step uses: 0 (automatic) means the single-pass form for
+// D3Q27 and the two-pass form for D2Q9.
+int effective_kernel(const elbm_solver* s)
+{
+    if (s->kernel != 0) return s->kernel;
+    return s->D == 3 ? 3 : 1;
+}
+
+size_t population_bytes(const elbm_solver* s)
+{
+    // 16 bytes of tail padding: 16-bit populations are staged as the 4-byte
+    // word that contains them, which for the last one reaches past the array
+    return (size_t)s->Q * s->N * elbm::storage_bytes(s->storage) + 16;
+}
+
+// The single-pass form needs a second population array.
+int ensure_second_array(elbm_solver* s, int kernel)
+{
+    const int k = kernel != 0 ? kernel : (s->D == 3 ? 3 : 1);
+    if (k != 3 || s->f2) return ELBM_OK;
+    cudaError_t e = cudaMalloc(&s->f2, population_bytes(s));
+    if (e != cudaSuccess) {
+        s->f2 = nullptr;
+        return cuda_fail(e, "second population array");
+    }
+    s->bytes += population_bytes(s);
+    return ELBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -225,9 +254,8 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
 
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
-    const size_t fbytes = (size_t)lattice * N * elbm::storage_bytes(storage);
     const size_t qbytes = (size_t)D * N * sizeof(float);
-    if (e == cudaSuccess) e = cudaMalloc(&s->f, fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->f, population_bytes(s));
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->q, qbytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int));
@@ -247,7 +275,12 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
         elbm_destroy(s);
         return rc;
     }
-    s->bytes = fbytes + qbytes + s->pipe.sync_words * sizeof(unsigned);
+    s->bytes = population_bytes(s) + qbytes + s->pipe.sync_words * sizeof(unsigned);
+    const int rc = ensure_second_array(s, s->kernel);
+    if (rc != ELBM_OK) {
+        elbm_destroy(s);
+        return rc;
+    }
     *out = s;
     return ELBM_OK;
 }
@@ -257,6 +290,7 @@ void elbm_destroy(elbm_solver* s)
     if (!s) return;
     if (s->stream || s->f) cudaStreamSynchronize(s->stream);
     cudaFree(s->f);
+    cudaFree(s->f2);
     cudaFree(s->q);
     cudaFree(s->sync);
     cudaFree(s->status);
@@ -275,11 +309,16 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "equilibrium must be 0 or 1");
             s->eq_mode = (int)value;
             return ELBM_OK;
-        case ELBM_OPT_KERNEL:
-            if (value != 0.0 && value != 1.0 && value != 2.0) return fail(ELBM_ERR_ARG, "kernel must be 0, 1 or 2");
+        case ELBM_OPT_KERNEL: {
+            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2 or 3");
             if (value == 2.0 && !pipelined_usable(s)) return fail(ELBM_ERR_ARG, "pipelined kernel unavailable");
+            if (value == 3.0 && s->D != 3) return fail(ELBM_ERR_ARG, "the single-pass kernel is D3Q27 only");
+            const int rc = ensure_second_array(s, (int)value);
+            if (rc != ELBM_OK) return rc;
             s->kernel = (int)value;
             return ELBM_OK;
+        }
         case ELBM_OPT_RHO_REF:
             if (!(value > 0.0) || !std::isfinite(value)) return fail(ELBM_ERR_ARG, "rho_ref must be > 0");
             if (s->initialised) return fail(ELBM_ERR_STATE, "rho_ref must be set before init");
@@ -379,17 +418,23 @@ int elbm_step(elbm_solver* s, int n)
     if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
     if (n < 0) return fail(ELBM_ERR_ARG, "n must be >= 0");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_step before elbm_init");
-    const bool pipelined = (s->kernel == 2) && pipelined_usable(s);
+    const int kernel = effective_kernel(s);
     cudaError_t e = cudaSuccess;
     int left = n;
     while (left > 0 && e == cudaSuccess) {
-        if (pipelined) {
+        if (kernel == 3 && s->parity == 0 && s->f2) {
+            // single pass: own-location state in f, result in f2, then swap
+            e = elbm::step_single_impl<3>(*s, s->f2, &s->launches);
+            std::swap(s->f, s->f2);
+            --left;
+        } else if (kernel == 2 && pipelined_usable(s)) {
             const int k = std::min(left, kStepsPerLaunch);
             e = (s->D == 2) ? elbm::step_pipelined_impl<2>(*s, s->parity, k, &s->launches)
                             : elbm::step_pipelined_impl<3>(*s, s->parity, k, &s->launches);
             s->parity = (s->parity + k) & 1;
             left -= k;
         } else {
+            // two-pass (also brings an odd-parity state back to the own-location layout)
             e = (s->D == 2) ? elbm::step_two_pass_impl<2>(*s, s->parity, &s->launches)
                             : elbm::step_two_pass_impl<3>(*s, s->parity, &s->launches);
             s->parity ^= 1;

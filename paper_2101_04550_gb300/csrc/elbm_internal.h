@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
-#include "../../include/elbm.h"
+#include "elbm.h"
 
 namespace elbm {
 
@@ -74,14 +74,15 @@ struct Solver {
     double u_ref[3] = {0, 0, 0};   // storage baseline velocity U0 (shifted storage modes)
     int u_ref_auto = 0;            // 1: U0 = mean velocity of the field given to elbm_init
     int eq_mode = 0;
-    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined
+    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined, 3 single pass (two arrays)
     int walls_y = 0;
     int parity = 0;
     int initialised = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
-    void* f = nullptr;                // populations
+    void* f = nullptr;                // populations (current)
+    void* f2 = nullptr;               // second population array of the single-pass form
     float* q = nullptr;               // anomaly field
     unsigned int* sync = nullptr;     // pipelined-kernel ticket, counters, phase order
     PipeGeom pipe;
@@ -104,6 +105,7 @@ void fill_params(const Solver& s, StepParams& p);
 // number of kernel launches it issued to *launches.
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_pipelined_impl(const Solver&, int, int, long long*);
+template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 template <int D> PipeGeom pipelined_geometry_impl(const Solver&);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);

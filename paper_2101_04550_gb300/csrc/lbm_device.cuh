@@ -150,6 +150,58 @@ __device__ __forceinline__ void scatter(const StepParams& p, const Node& n, cons
     }
 }
 
+// ---------------------------------------------- shared-memory staged gather
+// The populations of a node are copied asynchronously (cp.async, no register
+// cost) into the calling thread's column of a [Q][kStageStride] shared-memory
+// stage, then read back twice (moments, relaxation).  Copies move 4-byte
+// words; a 16-bit population is taken from the word that contains it, so the
+// population array carries 16 bytes of tail padding.
+__device__ __forceinline__ void cp_async4(unsigned* smem_dst, const void* gmem_src)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+// An integer the compiler must treat as unknown: recomputing an address from
+// it is cheaper than keeping 27 addresses alive across the collision.
+__device__ __forceinline__ int opaque(int x)
+{
+    asm volatile("" : "+r"(x));
+    return x;
+}
+
+// Fresh read of a staged word (volatile, so that the two read-backs of a
+// population are not merged into one long-lived register).
+__device__ __forceinline__ unsigned ld_stage(const unsigned* smem)
+{
+    unsigned v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(smem)));
+    return v;
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int ST>
+__device__ __forceinline__ const void* stage_src(const StepParams& p, int idx)
+{
+    using S = Storage<ST>;
+    if (sizeof(typename S::T) == 4) return static_cast<const float*>(p.f) + idx;
+    return static_cast<const unsigned*>(p.f) + (idx >> 1);
+}
+
+// Value of the population staged from element idx (deviation g_i).
+template <int ST>
+__device__ __forceinline__ float stage_value(const StepParams& p, unsigned word, int idx, int i)
+{
+    using S = Storage<ST>;
+    float v;
+    if (ST == ELBM_F16_SHIFT) v = __half2float(__ushort_as_half((unsigned short)(word >> ((idx & 1) * 16))));
+    else if (ST == ELBM_BF16_SHIFT) v = __bfloat162float(__ushort_as_bfloat16((unsigned short)(word >> ((idx & 1) * 16))));
+    else v = __uint_as_float(word);
+    return S::shifted ? v : v - p.bw[i] * p.rho_ref;
+}
+
 // ------------------------------------------------------------------ moments
 // drho = sum_i g_i (so rho = rho_ref + drho, Eq. density, since sum_i b_i = 1);
 // j_a = rho_ref U0_a + lam_a sum_i c_ia g_i = rho u_a (Eq. momentum, since the

@@ -12,18 +12,16 @@
 //     A(K-1), A(0), ..., A(L), C(0), A(L+1), C(1), A(L+2), ...
 // so that A(c) runs L chunks ahead of C(c) and the re-read of chunk c hits L2.
 //
-// One launch advances one time step.  Work is split into tiles and handed out
-// by an atomic ticket.  A collide tile of chunk c waits (bounded) for the
+// One launch advances one time step.  Work is split into warp-sized tiles,
+// numbered in phase order.  A collide tile of chunk c waits (bounded) for the
 // anomaly phases of chunks c-1, c and c+1 to be complete; with the phase order
-// above those have smaller tickets.  This covers every hazard of the in-place
-// slots and of the q field: the anomaly phase of c reads the slot set of c
-// before the collide phase of c rewrites it, slot sets of distinct nodes are
-// disjoint, and q of chunks c-1..c+1 is complete before C(c) reads it.  The
-// kernel boundary orders consecutive steps.
-// Because the oldest unfinished tile never waits, progress is guaranteed even
-// if not all blocks are resident.  Every wait is bounded by a wall-clock limit
-// after which the kernel records ELBM_ERR_TIMEOUT in the status word and all
-// blocks return.
+// above those tiles have smaller numbers.  This covers every hazard of the
+// in-place slots and of the q field: the anomaly phase of c reads the slot set
+// of c before the collide phase of c rewrites it, slot sets of distinct nodes
+// are disjoint, and q of chunks c-1..c+1 is complete before C(c) reads it.
+// The kernel boundary orders consecutive steps.  Every wait is bounded by a
+// wall-clock limit after which the kernel records ELBM_ERR_TIMEOUT in the
+// status word and all warps return.
 #pragma once
 #include <algorithm>
 
@@ -36,17 +34,17 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 // Resident blocks per SM the pipelined kernel is compiled for (register cap
 // 65536 / (256 * ELBM_PIPE_MIN_BLOCKS)).
 #ifndef ELBM_PIPE_MIN_BLOCKS
-#define ELBM_PIPE_MIN_BLOCKS 2
+#define ELBM_PIPE_MIN_BLOCKS ELBM_COLLIDE_MIN_BLOCKS
 #endif
-// Nodes per thread in one tile of the pipelined kernel.
+// Nodes per lane in one (warp-sized) tile of the pipelined kernel.
 #ifndef ELBM_PIPE_TILE_CPT
-#define ELBM_PIPE_TILE_CPT 4
+#define ELBM_PIPE_TILE_CPT 8
 #endif
 
 // Layout of the sync words (the first 2 + 2K are reset by the host before
-// every launch): [0] ticket, [1] abort flag, [2 .. 2+K) anomaly-phase
-// completions per chunk, [2+K .. 2+2K) collide-phase completions per chunk,
-// then 2 words per phase of the step: (type, chunk).
+// every launch): [0] unused, [1] abort flag, [2 .. 2+K) anomaly-phase
+// completions per chunk, [2+K .. 2+2K) unused, then 2 words per phase of the
+// step: (type, chunk).
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
 {
     unsigned v;
@@ -97,44 +95,42 @@ __device__ __forceinline__ bool wait3_ge(const StepParams& p, const unsigned* a,
     }
 }
 
-// One time step (streaming parity PAR) over the whole grid.  Thread 0 of a
-// block fetches the next ticket while the block works on the current tile, so
-// the atomic's latency is hidden; a block holding tickets t < t' only ever
-// waits for tickets below t, so the deadlock-freedom argument is unchanged.
+// One time step (streaming parity PAR) over the whole grid.  Every warp is an
+// independent worker with a static share of the tiles: warp w of W processes
+// tiles w, w + W, w + 2W, ... in issue order.  Lane 0 waits for a tile's
+// dependencies; after __syncwarp() it publishes the tile's completion with a
+// release add.  No block-wide barrier and no ticket atomic is needed.  The
+// kernel is launched cooperatively, so all W warps are resident; the warp that
+// owns the oldest unfinished tile has finished all its earlier tiles and that
+// tile only waits for older ones, so it never waits and the step completes.
 template <int D, int ST, int PAR>
 __global__ void __launch_bounds__(kBlock, ELBM_PIPE_MIN_BLOCKS) k_pipelined(StepParams p)
 {
-    __shared__ int s_next;
-    __shared__ int s_ok;
+    __shared__ unsigned stage[Lat<D>::Q * kBlock];
+    const int lane = threadIdx.x & 31;
     const int K = p.nchunks, T = p.tiles_per_chunk;
     unsigned* done_a = p.sync + 2;
-    unsigned* done_c = p.sync + 2 + K;
     const unsigned* order = p.sync + 2 + 2 * K;
     const int layer = (D == 3) ? p.plane : p.nx;
     const int chunk_cells = p.chunk_planes * layer;
     const int total = 2 * K * T;
+    const int W = gridDim.x * (kBlock / 32);
 
-    if (threadIdx.x == 0) s_next = (int)atomicAdd(p.sync, 1u);
-    __syncthreads();
-    int t = s_next;
-    while (t < total) {
+    for (int t = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); t < total; t += W) {
         const int tile = t % T;
         const int ph = t / T;
         const int type = (int)order[2 * ph];  // 0 anomaly phase, 1 collide phase
         const int c = (int)order[2 * ph + 1];
-        __syncthreads();  // every thread has read s_next before it is rewritten
-        if (threadIdx.x == 0) {
-            s_next = (int)atomicAdd(p.sync, 1u);
-            bool ok = true;
-            if (type == 1) {
+        if (type == 1) {
+            int ok = 1;
+            if (lane == 0) {
                 const int cm = (c == 0) ? K - 1 : c - 1, cp = (c == K - 1) ? 0 : c + 1;
                 ok = wait3_ge(p, done_a + cm, done_a + c, done_a + cp, (unsigned)T);
             }
-            s_ok = ok;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            __syncwarp();  // the other lanes' reads are ordered after lane 0's acquire
         }
-        __syncthreads();
-        if (!s_ok) break;
-        const int t_next = s_next;
 
         const int c_begin = c * chunk_cells;
         const int c_end = min(p.N, c_begin + chunk_cells);
@@ -142,7 +138,7 @@ __global__ void __launch_bounds__(kBlock, ELBM_PIPE_MIN_BLOCKS) k_pipelined(Step
         const int t_end = min(c_end, t_begin + p.tile_cells);
         if (type == 0) {
 #pragma unroll 1
-            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock) {
+            for (int cell = t_begin + lane; cell < t_end; cell += 32) {
                 const Node n = make_node<D>(p, cell);
                 float g[Lat<D>::Q];
                 gather<D, ST, PAR>(p, n, g);
@@ -154,12 +150,13 @@ __global__ void __launch_bounds__(kBlock, ELBM_PIPE_MIN_BLOCKS) k_pipelined(Step
             }
         } else {
 #pragma unroll 1
-            for (int cell = t_begin + threadIdx.x; cell < t_end; cell += kBlock)
-                collide_node<D, ST, PAR>(p, cell);
+            for (int cell = t_begin + lane; cell < t_end; cell += 32)
+                collide_staged<D, ST, PAR>(p, cell, stage + threadIdx.x);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) red_release_add((type == 0 ? done_a : done_c) + c, 1u);
-        t = t_next;
+        if (type == 0) {  // collide completions are not waited on within a step
+            __syncwarp();
+            if (lane == 0) red_release_add(done_a + c, 1u);
+        }
     }
 }
 
@@ -190,10 +187,12 @@ PipeGeom pipelined_geometry_impl(const Solver& s)
     g.grid = pipelined_grid_impl<D>(s);
     g.chunk_planes = std::max(1, std::min(nlayers, (65536 + layer - 1) / layer));
     g.nchunks = (nlayers + g.chunk_planes - 1) / g.chunk_planes;
-    g.tile_cells = ELBM_PIPE_TILE_CPT * kBlock;
+    g.tile_cells = ELBM_PIPE_TILE_CPT * 32;
     const int chunk_cells = g.chunk_planes * layer;
     g.tiles_per_chunk = (chunk_cells + g.tile_cells - 1) / g.tile_cells;
-    const int L = (g.grid + 2 * g.tiles_per_chunk - 1) / (2 * g.tiles_per_chunk) + 1;
+    // tiles in flight: one per resident warp
+    const int warps = g.grid * (kBlock / 32);
+    const int L = (warps + 2 * g.tiles_per_chunk - 1) / (2 * g.tiles_per_chunk) + 1;
     g.lookahead = (g.nchunks >= 3) ? std::max(1, std::min(L, g.nchunks - 2)) : 0;
     g.sync_words = 2 + 2 * (size_t)g.nchunks + 4 * (size_t)g.nchunks;
     return g;
@@ -216,10 +215,12 @@ cudaError_t step_pipelined_impl(const Solver& s, int parity, int nsteps, long lo
         p.parity = (parity + k) & 1;
         cudaError_t e = cudaMemsetAsync(s.sync, 0, (2 + 2 * (size_t)g.nchunks) * sizeof(unsigned), s.stream);
         if (e != cudaSuccess) return e;
+        void* args[] = {&p};
         ELBM_DISPATCH_STORAGE(s.storage, {
-            if (p.parity == 0) k_pipelined<D, ST, 0><<<g.grid, kBlock, 0, s.stream>>>(p);
-            else k_pipelined<D, ST, 1><<<g.grid, kBlock, 0, s.stream>>>(p);
+            const void* fn = (p.parity == 0) ? (const void*)k_pipelined<D, ST, 0> : (const void*)k_pipelined<D, ST, 1>;
+            e = cudaLaunchCooperativeKernel(fn, dim3(g.grid), dim3(kBlock), args, 0, s.stream);
         });
+        if (e != cudaSuccess) return e;
         ++*launches;
     }
     return cudaGetLastError();

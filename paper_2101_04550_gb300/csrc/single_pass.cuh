@@ -1,0 +1,218 @@
+// Single-pass form of the extended LBGK step with two population arrays.
+//
+// The correction term needs the anomaly Q~_aaa of the face neighbours at the
+// same time level (Eq. Paastar1).  With a read-only source array and a
+// separate destination, every block can recompute the anomaly of the nodes
+// around its own tile, so one pass and one read of the populations suffice.
+//
+// State: `src` holds the post-streaming populations of every node at the
+// node's own location (the layout of the in-place form's even parity).  A step
+// reads src[i][x], relaxes, and pushes f'_i(x) to dst[i][x + c_i] (Eq. LBGK);
+// then the arrays swap roles.
+//
+// Geometry (D3Q27): a block of kBlock = 256 threads owns a tile of 32 x 8
+// columns and marches through a segment of kSegPlanes z planes.  Per plane k
+// it (1) stages the populations of plane k+1 of its tile and of the 80-node
+// ring around it (2 columns x 8 and 2 rows x 32) in shared memory with
+// cp.async, (2) computes the anomaly of those nodes -- x and y components into
+// a 3-deep ring of plane buffers with a one-node halo, the z component of its
+// own node into a register, (3) after one barrier relaxes the nodes of plane
+// k, whose populations were staged one plane earlier, using the anomaly of
+// plane k (x, y differences) and of planes k-1, k+1 (z difference).  Threads
+// whose column lies beyond a ragged grid edge take the periodic image of
+// their position: they supply the anomaly of the wrapped node and relax nothing.
+#pragma once
+#include "step_kernels.cuh"
+
+namespace elbm {
+
+constexpr int kTileX = 32, kTileY = 8;   // kTileX * kTileY == kBlock
+constexpr int kHalo = 2 * kTileX + 2 * kTileY;
+constexpr int kSegPlanes = 32;
+
+#ifndef ELBM_SINGLE_MIN_BLOCKS
+#define ELBM_SINGLE_MIN_BLOCKS 3
+#endif
+
+struct SingleSmem {
+    unsigned stage[2][27][kBlock];         // populations of the tile, planes k and k+1
+    unsigned halo_stage[27][kHalo];        // populations of the ring, plane k+1
+    float qx[3][kTileY][kTileX + 2];       // Q~_xxx with an x halo, planes k, k+1, k+2 (ring)
+    float qy[3][kTileY + 2][kTileX];       // Q~_yyy with a y halo
+};
+
+// Anomaly components of a node whose 27 populations were staged with stride
+// `stride` (the sums of moments(), then Eq. Deviation).
+template <int ST>
+__device__ __forceinline__ void staged_anomaly(const StepParams& p, const unsigned* col, int stride,
+                                               unsigned halves, float* q)
+{
+    auto gval = [&](int i) { return stage_value<ST>(p, ld_stage(col + i * stride), (int)((halves >> i) & 1u), i); };
+    float drho, j[3];
+    moments_of<3>(p, gval, drho, j);
+    const float inv_rho = 1.0f / (p.rho_ref + drho);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = anomaly(p, a, j[a], j[a] * inv_rho);
+}
+
+// Issue the cp.async copies of the 27 own-location populations of node `cell`
+// into a staged column; returns the half-word selector bits.
+template <int ST>
+__device__ __forceinline__ unsigned stage_node(const StepParams& p, int cell, unsigned* col, int stride)
+{
+    unsigned halves = 0;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+        const int idx = i * p.N + cell;
+        halves |= (unsigned)(idx & 1) << i;
+        cp_async4(col + i * stride, stage_src<ST>(p, idx));
+    }
+    return halves;
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ int modi(int v, int n) { return ((v % n) + n) % n; }
+
+template <int ST>
+__global__ void __launch_bounds__(kBlock, ELBM_SINGLE_MIN_BLOCKS) k_single_pass(StepParams p, void* dst)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SingleSmem& sm = *reinterpret_cast<SingleSmem*>(smem_raw);
+    using S = Storage<ST>;
+    const int tx = threadIdx.x & (kTileX - 1), ty = threadIdx.x / kTileX;
+    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+    const int z0 = blockIdx.z * kSegPlanes;
+    const int z1 = min(p.nz, z0 + kSegPlanes);
+    const bool active = (x0 + tx < p.nx) && (y0 + ty < p.ny);
+    const int gx = modi(x0 + tx, p.nx), gy = modi(y0 + ty, p.ny);  // periodic image beyond a ragged edge
+    const int col_off = gx + gy * p.nx;
+
+    // ring node handled by this thread (threads 0 .. kHalo-1): rows y0-1 and
+    // y0+kTileY for the y anomaly, columns x0-1 and x0+kTileX for the x anomaly
+    int hx = 0, hy = 0, hslot = -1;
+    if (threadIdx.x < 2 * kTileX) {
+        hx = x0 + (threadIdx.x & (kTileX - 1));
+        hy = (threadIdx.x < kTileX) ? y0 - 1 : y0 + kTileY;
+        hslot = threadIdx.x;
+    } else if (threadIdx.x < kHalo) {
+        const int k = threadIdx.x - 2 * kTileX;
+        hx = (k < kTileY) ? x0 - 1 : x0 + kTileX;
+        hy = y0 + (k & (kTileY - 1));
+        hslot = threadIdx.x;
+    }
+    const int h_off = modi(hx, p.nx) + modi(hy, p.ny) * p.nx;
+
+    auto plane_of = [&](int z) { return wrapi(z, p.nz) * p.plane; };
+
+    // Stage plane z of the tile (into stage[b]) and of the ring, compute the
+    // anomaly into ring slot qs; returns this thread's Q~_zzz.
+    auto anomaly_plane = [&](int z, int b, int qs) -> float {
+        const int base = plane_of(z);
+        const unsigned halves = stage_node<ST>(p, base + col_off, &sm.stage[b][0][threadIdx.x], kBlock);
+        unsigned hhalves = 0;
+        if (hslot >= 0) hhalves = stage_node<ST>(p, base + h_off, &sm.halo_stage[0][hslot], kHalo);
+        cp_async_wait_all();
+        float q[3];
+        staged_anomaly<ST>(p, &sm.stage[b][0][threadIdx.x], kBlock, halves, q);
+        sm.qx[qs][ty][tx + 1] = q[0];
+        sm.qy[qs][ty + 1][tx] = q[1];
+        if (hslot >= 0) {
+            float qh[3];
+            staged_anomaly<ST>(p, &sm.halo_stage[0][hslot], kHalo, hhalves, qh);
+            if (hslot < kTileX) sm.qy[qs][0][hslot] = qh[1];
+            else if (hslot < 2 * kTileX) sm.qy[qs][kTileY + 1][hslot - kTileX] = qh[1];
+            else {
+                const int k = hslot - 2 * kTileX;
+                if (k < kTileY) sm.qx[qs][k][0] = qh[0];
+                else sm.qx[qs][k - kTileY][kTileX + 1] = qh[0];
+            }
+        }
+        return q[2];
+    };
+
+    // prologue: Q~_zzz of plane z0-1 (own column only) and everything of plane z0
+    float qz_prev;
+    {
+        const unsigned halves = stage_node<ST>(p, plane_of(z0 - 1) + col_off, &sm.stage[1][0][threadIdx.x], kBlock);
+        cp_async_wait_all();
+        float q[3];
+        staged_anomaly<ST>(p, &sm.stage[1][0][threadIdx.x], kBlock, halves, q);
+        qz_prev = q[2];
+    }
+    float qz_cur = anomaly_plane(z0, 0, 0);
+    unsigned cur_halves = 0;
+    {
+        const int idx0 = plane_of(z0) + col_off;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) cur_halves |= (unsigned)((i * p.N + idx0) & 1) << i;
+    }
+
+    typename S::T* out = static_cast<typename S::T*>(dst);
+    for (int z = z0, m = 0; z < z1; ++z, ++m) {
+        const int b = m & 1, qs = m % 3;
+        // plane z+1: stage and anomaly (ring slot (m+1) % 3)
+        const float qz_next = anomaly_plane(z + 1, b ^ 1, (m + 1) % 3);
+        const int idx_next = plane_of(z + 1) + col_off;
+        __syncthreads();
+        if (active) {
+            // relax node (gx, gy, z) from stage[b]
+            const unsigned* col = &sm.stage[b][0][threadIdx.x];
+            auto gval = [&](int i) {
+                return stage_value<ST>(p, ld_stage(col + i * kBlock), (int)((cur_halves >> i) & 1u), i);
+            };
+            float drho, j[3];
+            moments_of<3>(p, gval, drho, j);
+            float d[3] = {0.f, 0.f, 0.f};
+            if (p.eq_mode == 0) {
+                d[0] = (sm.qx[qs][ty][tx + 2] - sm.qx[qs][ty][tx]) * p.inv_2lam[0];
+                d[1] = (sm.qy[qs][ty + 2][tx] - sm.qy[qs][ty][tx]) * p.inv_2lam[1];
+                d[2] = (qz_next - qz_prev) * p.inv_2lam[2];
+            }
+            // push targets: node (gx + cx, gy + cy, z + cz), periodic
+            const int xo[3] = {gx == 0 ? p.nx - 1 : gx - 1, gx, gx == p.nx - 1 ? 0 : gx + 1};
+            const int yo[3] = {(gy == 0 ? p.ny - 1 : gy - 1) * p.nx, gy * p.nx, (gy == p.ny - 1 ? 0 : gy + 1) * p.nx};
+            const int zo[3] = {plane_of(z - 1), plane_of(z), plane_of(z + 1)};
+            auto put = [&](int i, float gn) {
+                const int slot = opaque(i * p.N) + xo[cx_of(i) + 1] + yo[cy_of(i) + 1] + zo[cz_of<3>(i) + 1];
+                S::store(out + slot, S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn));
+            };
+            relax_streamed<3>(p, gval, put, drho, j, d);
+        }
+        qz_prev = qz_cur;
+        qz_cur = qz_next;
+        cur_halves = 0;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) cur_halves |= (unsigned)((i * p.N + idx_next) & 1) << i;
+    }
+}
+
+inline size_t single_pass_smem() { return sizeof(SingleSmem); }
+
+// One single-pass step from s.f into dst (D3Q27 only; the caller swaps the arrays).
+template <int D>
+cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
+{
+    if constexpr (D != 3) {
+        (void)s;
+        (void)dst;
+        (void)launches;
+        return cudaErrorNotSupported;
+    } else {
+        StepParams p;
+        fill_params(s, p);
+        p.parity = 0;
+        const dim3 grid((unsigned)((s.nx + kTileX - 1) / kTileX), (unsigned)((s.ny + kTileY - 1) / kTileY),
+                        (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
+        const size_t smem = sizeof(SingleSmem);
+        cudaError_t e = cudaSuccess;
+        ELBM_DISPATCH_STORAGE(s.storage, {
+            e = cudaFuncSetAttribute(k_single_pass<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) k_single_pass<ST><<<grid, kBlock, smem, s.stream>>>(p, dst);
+        });
+        if (e != cudaSuccess) return e;
+        ++*launches;
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace elbm

@@ -10,6 +10,11 @@ namespace elbm {
 
 constexpr int kBlock = 256;
 
+// Resident blocks per SM the collide kernels are compiled for.
+#ifndef ELBM_COLLIDE_MIN_BLOCKS
+#define ELBM_COLLIDE_MIN_BLOCKS 4
+#endif
+
 #define ELBM_DISPATCH_STORAGE(storage, ...)                              \
     switch (storage) {                                                   \
         case ELBM_F32: { constexpr int ST = ELBM_F32; __VA_ARGS__; } break;             \
@@ -37,17 +42,95 @@ __global__ void __launch_bounds__(kBlock) k_anomaly(StepParams p)
     for (int a = 0; a < D; ++a) p.q[a * p.N + cell] = anomaly(p, a, j[a], j[a] * inv_rho);
 }
 
-// The per-node update once the anomaly field of this time level is complete:
-// central difference of q along each axis (Eq. Paastar1), extended
-// equilibrium, relaxation, write-back in place.
-template <int D, int ST, int PAR>
-__device__ __forceinline__ void collide_node(const StepParams& p, int cell)
+// Moments of a node from a population accessor gval(i) (the sums of moments()).
+template <int D, typename G>
+__device__ __forceinline__ void moments_of(const StepParams& p, G&& gval, float& drho, float* j)
 {
+    float r = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Lat<D>::Q; ++i) {
+        const float gi = gval(i);
+        r += gi;
+        if (cx_of(i) == 1) sx += gi;
+        if (cx_of(i) == -1) sx -= gi;
+        if (cy_of(i) == 1) sy += gi;
+        if (cy_of(i) == -1) sy -= gi;
+        if (cz_of<D>(i) == 1) sz += gi;
+        if (cz_of<D>(i) == -1) sz -= gi;
+    }
+    drho = r;
+    j[0] = fmaf(p.lam[0], sx, p.j0[0]);
+    j[1] = fmaf(p.lam[1], sy, p.j0[1]);
+    j[2] = (D == 3) ? fmaf(p.lam[2], sz, p.j0[2]) : 0.f;
+}
+
+// Relaxation of one node toward the extended equilibrium with the
+// conservation correction of relax(), for populations read through gval(i)
+// (read twice, not kept in registers) and results handed to put(i, g'_i).
+template <int D, typename G, typename P>
+__device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&& put, float drho,
+                                               const float* j, const float* d)
+{
+    constexpr int I0 = (Lat<D>::Q - 1) / 2;
+    const float rho = p.rho_ref + drho;
+    const float inv_rho = 1.0f / rho;
+    float u[3], pcorr[3], du[3], dP[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = j[a] * inv_rho;
+        pcorr[a] = p.coef * inv_rho * d[a];
+    }
+    baseline_args<D>(p, u, pcorr, du, dP);
+    const float om = p.omega;
+    float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    float keep[2 * D + 1];
+    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
+        const float gi = gval(i);
+        const float dl = geq - gi;
+        e0 += dl;
+        if (cx_of(i) == 1) ex += dl;
+        if (cx_of(i) == -1) ex -= dl;
+        if (cy_of(i) == 1) ey += dl;
+        if (cy_of(i) == -1) ey -= dl;
+        if (cz_of<D>(i) == 1) ez += dl;
+        if (cz_of<D>(i) == -1) ez -= dl;
+        const int k = corrected_slot<D>(i);
+        if (k >= 0) keep[k] = geq;
+        else put(i, fmaf(om, dl, gi));
+    });
+    const float hx = 0.5f * ex, hy = 0.5f * ey;
+    put(I0, fmaf(om, (keep[0] - gval(I0)) - e0, gval(I0)));
+    put(I0 - 1, fmaf(om, (keep[1] - gval(I0 - 1)) + hx, gval(I0 - 1)));
+    put(I0 + 1, fmaf(om, (keep[2] - gval(I0 + 1)) - hx, gval(I0 + 1)));
+    put(I0 - 3, fmaf(om, (keep[3] - gval(I0 - 3)) + hy, gval(I0 - 3)));
+    put(I0 + 3, fmaf(om, (keep[4] - gval(I0 + 3)) - hy, gval(I0 + 3)));
+    if (D == 3) {
+        const float hz = 0.5f * ez;
+        put(I0 - 9, fmaf(om, (keep[5] - gval(I0 - 9)) + hz, gval(I0 - 9)));
+        put(I0 + 9, fmaf(om, (keep[6] - gval(I0 + 9)) - hz, gval(I0 + 9)));
+    }
+}
+
+// The per-node update once the anomaly field of this time level is complete:
+// gather the post-streaming populations into the thread's shared-memory
+// column `col` (stride kBlock), central difference of q along each axis
+// (Eq. Paastar1), extended equilibrium, relaxation, write-back in place.
+// Populations are read back from the stage instead of being held in
+// registers, which keeps the register count low enough for 32 resident
+// warps per SM.
+template <int D, int ST, int PAR>
+__device__ __forceinline__ void collide_staged(const StepParams& p, int cell, unsigned* col)
+{
+    constexpr int Q = Lat<D>::Q;
+    using S = Storage<ST>;
     const Node n = make_node<D>(p, cell);
-    float g[Lat<D>::Q];
-    gather<D, ST, PAR>(p, n, g);
-    float drho, j[3];
-    moments<D>(p, g, drho, j);
+    unsigned halves = 0;  // bit i: population i sits in the upper half of its staged word
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int idx = read_slot<D>(n, p.N, i, PAR);
+        halves |= (unsigned)(idx & 1) << i;
+        cp_async4(col + i * kBlock, stage_src<ST>(p, idx));
+    }
     float d[3] = {0.f, 0.f, 0.f};
     if (p.eq_mode == 0) {
         const float* q = p.q;
@@ -55,17 +138,27 @@ __device__ __forceinline__ void collide_node(const StepParams& p, int cell)
         d[1] = (q[p.N + n.at(0, 1, 0)] - q[p.N + n.at(0, -1, 0)]) * p.inv_2lam[1];
         if (D == 3) d[2] = (q[2 * p.N + n.at(0, 0, 1)] - q[2 * p.N + n.at(0, 0, -1)]) * p.inv_2lam[2];
     }
-    relax<D>(p, g, drho, j, d);
-    scatter<D, ST, PAR>(p, n, g);
+    cp_async_wait_all();
+    auto gval = [&](int i) { return stage_value<ST>(p, ld_stage(col + i * kBlock), (int)((halves >> i) & 1u), i); };
+    float drho, j[3];
+    moments_of<D>(p, gval, drho, j);
+    typename S::T* f = static_cast<typename S::T*>(p.f);
+    const int cell_o = opaque(cell);
+    auto put = [&](int i, float gn) {
+        const int slot = (PAR == 0) ? (Q - 1 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
+        S::store(f + slot, S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn));
+    };
+    relax_streamed<D>(p, gval, put, drho, j, d);
 }
 
-// Pass 2 over every node.
+// Pass 2 over every node: one node per thread, populations staged in shared memory.
 template <int D, int ST, int PAR>
-__global__ void __launch_bounds__(kBlock) k_collide(StepParams p)
+__global__ void __launch_bounds__(kBlock, ELBM_COLLIDE_MIN_BLOCKS) k_collide(StepParams p)
 {
+    __shared__ unsigned stage[Lat<D>::Q * kBlock];
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
-    collide_node<D, ST, PAR>(p, cell);
+    collide_staged<D, ST, PAR>(p, cell, stage + threadIdx.x);
 }
 
 template <int D>
@@ -75,13 +168,14 @@ cudaError_t step_two_pass_impl(const Solver& s, int parity, long long* launches)
     fill_params(s, p);
     p.parity = parity;
     const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
+    const dim3 cgrid = grid;
     ELBM_DISPATCH_STORAGE(s.storage, {
         if (parity == 0) {
             if (p.eq_mode == 0) { k_anomaly<D, ST, 0><<<grid, kBlock, 0, s.stream>>>(p); ++*launches; }
-            k_collide<D, ST, 0><<<grid, kBlock, 0, s.stream>>>(p);
+            k_collide<D, ST, 0><<<cgrid, kBlock, 0, s.stream>>>(p);
         } else {
             if (p.eq_mode == 0) { k_anomaly<D, ST, 1><<<grid, kBlock, 0, s.stream>>>(p); ++*launches; }
-            k_collide<D, ST, 1><<<grid, kBlock, 0, s.stream>>>(p);
+            k_collide<D, ST, 1><<<cgrid, kBlock, 0, s.stream>>>(p);
         }
         ++*launches;
     });

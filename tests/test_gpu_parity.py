@@ -129,7 +129,7 @@ def test_d3q27_half_storage_turbulence(storage):
 
 
 # ----------------------------------------------------------- D3Q27 cases
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_d3q27_turbulence_ragged_stretched(kernel):
     """Seeded solenoidal field on a ragged 37x20x23 grid, lam = (1, 1.5, 2), T = 0.5."""
     n, lam = (37, 20, 23), (1.0, 1.5, 2.0)
@@ -161,11 +161,13 @@ def test_d3q27_minimum_grid():
 
 # ---------------------------------------------------- kernels and state
 @pytest.mark.parametrize("lattice,n", [(elbm.D3Q27, (64, 64, 48)), (elbm.D3Q27, (40, 24, 3)),
+                                       (elbm.D3Q27, (5, 3, 70)), (elbm.D3Q27, (70, 20, 33)),
                                        (elbm.D2Q9, (300, 700)), (elbm.D2Q9, (33, 5))])
-@pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT])
-def test_two_pass_and_pipelined_agree_bitwise(lattice, n, storage):
-    """Both kernel forms evaluate the same per-node arithmetic, so the states
-    agree bit for bit, across launches of several steps and both parities."""
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT, elbm.F32_SHIFT])
+def test_kernel_forms_agree_bitwise(lattice, n, storage):
+    """The two-pass, pipelined and (D3Q27) single-pass forms evaluate the same
+    per-node arithmetic, so the states agree bit for bit, across launches of
+    several steps and both streaming parities."""
     D = 2 if lattice == elbm.D2Q9 else 3
     if D == 3:
         rho, u = inputs.isotropic_turbulence(n, seed=2, k0=3.0, u_rms=0.05)
@@ -173,13 +175,14 @@ def test_two_pass_and_pipelined_agree_bitwise(lattice, n, storage):
         rho, u = inputs.double_shear_layer(n, U=0.1)
     lam = (1.0, 2.0, 1.0)
     outs = []
-    for kernel in (1, 2):
+    for kernel in ((1, 2, 3) if D == 3 else (1, 2)):
         with elbm.Solver(lattice, n, stretch=lam, T=0.5, nu=0.01, storage=storage, kernel=kernel) as s:
             s.init(rho, u)
             for k in (1, 2, 4):
                 s.step(k)
             outs.append(s.get_populations())
-    assert np.array_equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
 
 
 @pytest.mark.parametrize("lattice,n", [(elbm.D2Q9, (20, 12)), (elbm.D3Q27, (9, 7, 5))])
