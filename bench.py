@@ -34,6 +34,8 @@ WORKLOAD = dict(workload="D3Q27 decaying isotropic turbulence 256^3 periodic", l
                 nx=256, ny=256, nz=256, stretch=[1.0, 1.0, 1.0], T=1.0 / 3.0, nu=0.0233,
                 u_rms=0.08, k0=4.0, seed=0)
 FALLBACK_HBM_GBS = 6800.0
+KERNEL_NAMES = {0: "automatic", 1: "two-pass", 2: "pipelined", 3: "single-pass"}
+KERNEL_LAUNCHES = {0: "automatic", 1: "k_anomaly+k_collide", 2: "k_pipelined", 3: "k_single_pass"}
 # ncu DRAM bytes (read + write) per node update of the pipelined kernel,
 # keyed by the hash of the kernel sources they were measured on.
 MEASURED_TRAFFIC = {}
@@ -198,7 +200,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
-    ap.add_argument("--kernel", type=int, default=2, choices=[1, 2])
+    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 automatic, 1 two-pass in place, 2 pipelined in place, 3 single pass (two arrays)")
     ap.add_argument("--reduce-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -340,7 +343,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["workload"], "lattice": "D3Q27", "nodes": [w["nx"], w["ny"], w["nz"]],
-                       "storage": args.storage, "kernel": {1: "two-pass", 2: "pipelined"}[args.kernel],
+                       "storage": args.storage, "kernel": KERNEL_NAMES[args.kernel],
                        "T": w["T"], "nu": w["nu"], "u_rms": w["u_rms"],
                        "reduce_every": args.reduce_every, "global_batch": world,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
@@ -349,7 +352,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "kernel": "k_pipelined" if args.kernel == 2 else "k_anomaly+k_collide",
+                         "kernel": KERNEL_LAUNCHES[args.kernel],
                          "alg_bytes_per_node": alg_bytes_per_cell,
                          "kernel_ms_per_step": step_s / args.steps * 1e3},
             "e2e": {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",

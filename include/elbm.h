@@ -73,7 +73,11 @@ extern "C" {
 /* ELBM_OPT_KERNEL: 0 = automatic; 1 = two-pass (anomaly pass, collide pass);
  *   2 = pipelined pass (same arithmetic; one cooperative launch per step whose
  *   warps interleave the two phases chunk by chunk, so that the collide phase
- *   re-reads the populations from L2). */
+ *   re-reads the populations from L2);
+ *   3 = single pass with a second population array (D3Q27; each block
+ *   recomputes the anomaly around its tile, populations are read once);
+ *   4 = graph-pipelined passes (a CUDA graph of per-chunk anomaly and collide
+ *   kernels, so that the collide kernels re-read the populations from L2). */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3

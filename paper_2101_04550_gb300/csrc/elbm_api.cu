@@ -176,6 +176,16 @@ bool pipelined_usable(const elbm_solver* s) { return s->pipe.grid > 0 && s->sync
 
 bool shifted_storage_mode(int storage) { return storage != ELBM_F32; }
 
+// The graph-pipelined step bakes the parameter block into its kernel nodes;
+// any change of parameters drops the graphs (they are rebuilt on demand).
+void drop_graphs(elbm_solver* s)
+{
+    for (auto& g : s->graph_exec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
 // Kernel form a step uses: 0 (automatic) means the single-pass form for
 // D3Q27 and the two-pass form for D2Q9.
 int effective_kernel(const elbm_solver* s)
@@ -289,6 +299,7 @@ void elbm_destroy(elbm_solver* s)
 {
     if (!s) return;
     if (s->stream || s->f) cudaStreamSynchronize(s->stream);
+    drop_graphs(s);
     cudaFree(s->f);
     cudaFree(s->f2);
     cudaFree(s->q);
@@ -304,14 +315,15 @@ void elbm_destroy(elbm_solver* s)
 int elbm_set_option(elbm_solver* s, int key, double value)
 {
     if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
+    drop_graphs(s);
     switch (key) {
         case ELBM_OPT_EQUILIBRIUM:
             if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "equilibrium must be 0 or 1");
             s->eq_mode = (int)value;
             return ELBM_OK;
         case ELBM_OPT_KERNEL: {
-            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2 or 3");
+            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != 4.0)
+                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2, 3 or 4");
             if (value == 2.0 && !pipelined_usable(s)) return fail(ELBM_ERR_ARG, "pipelined kernel unavailable");
             if (value == 3.0 && s->D != 3) return fail(ELBM_ERR_ARG, "the single-pass kernel is D3Q27 only");
             const int rc = ensure_second_array(s, (int)value);
@@ -410,6 +422,7 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
     s->parity = 0;
     s->steps_done = 0;
     s->initialised = 1;
+    drop_graphs(s);
     return ELBM_OK;
 }
 
@@ -426,6 +439,16 @@ int elbm_step(elbm_solver* s, int n)
             // single pass: own-location state in f, result in f2, then swap
             e = elbm::step_single_impl<3>(*s, s->f2, &s->launches);
             std::swap(s->f, s->f2);
+            --left;
+        } else if (kernel == 4) {
+            if (!s->graph_exec[s->parity]) {
+                e = (s->D == 2) ? elbm::build_step_graph_impl<2>(*s, s->parity, &s->graph_exec[s->parity], &s->graph_nodes)
+                                : elbm::build_step_graph_impl<3>(*s, s->parity, &s->graph_exec[s->parity], &s->graph_nodes);
+                if (e != cudaSuccess) break;
+            }
+            e = cudaGraphLaunch(s->graph_exec[s->parity], s->stream);
+            s->launches += s->graph_nodes;
+            s->parity ^= 1;
             --left;
         } else if (kernel == 2 && pipelined_usable(s)) {
             const int k = std::min(left, kStepsPerLaunch);

@@ -74,7 +74,7 @@ struct Solver {
     double u_ref[3] = {0, 0, 0};   // storage baseline velocity U0 (shifted storage modes)
     int u_ref_auto = 0;            // 1: U0 = mean velocity of the field given to elbm_init
     int eq_mode = 0;
-    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined, 3 single pass (two arrays)
+    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined, 3 single pass (two arrays), 4 graph-pipelined
     int walls_y = 0;
     int parity = 0;
     int initialised = 0;
@@ -86,6 +86,8 @@ struct Solver {
     float* q = nullptr;               // anomaly field
     unsigned int* sync = nullptr;     // pipelined-kernel ticket, counters, phase order
     PipeGeom pipe;
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // graph-pipelined step per parity
+    int graph_nodes = 0;
     int* status = nullptr;            // device status word
     float* mom = nullptr;             // reduction scratch: rho, u[3], fmin per node
     double* partials = nullptr;       // reduction scratch: per-block FP64 partial sums
@@ -106,6 +108,7 @@ void fill_params(const Solver& s, StepParams& p);
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_pipelined_impl(const Solver&, int, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
+template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
 template <int D> PipeGeom pipelined_geometry_impl(const Solver&);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);

@@ -169,6 +169,13 @@ __device__ __forceinline__ int opaque(int x)
     return x;
 }
 
+// 16-byte asynchronous copy (global -> shared, both 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem_src) : "memory");
+}
+
 // Fresh read of a staged word (volatile, so that the two read-backs of a
 // population are not merged into one long-lived register).
 __device__ __forceinline__ unsigned ld_stage(const unsigned* smem)
@@ -181,6 +188,9 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most one committed group (the newest) is still in flight.
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int ST>
 __device__ __forceinline__ const void* stage_src(const StepParams& p, int idx)

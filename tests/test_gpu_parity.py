@@ -129,7 +129,7 @@ def test_d3q27_half_storage_turbulence(storage):
 
 
 # ----------------------------------------------------------- D3Q27 cases
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 def test_d3q27_turbulence_ragged_stretched(kernel):
     """Seeded solenoidal field on a ragged 37x20x23 grid, lam = (1, 1.5, 2), T = 0.5."""
     n, lam = (37, 20, 23), (1.0, 1.5, 2.0)
@@ -175,7 +175,7 @@ def test_kernel_forms_agree_bitwise(lattice, n, storage):
         rho, u = inputs.double_shear_layer(n, U=0.1)
     lam = (1.0, 2.0, 1.0)
     outs = []
-    for kernel in ((1, 2, 3) if D == 3 else (1, 2)):
+    for kernel in ((1, 2, 3, 4) if D == 3 else (1, 2, 4)):
         with elbm.Solver(lattice, n, stretch=lam, T=0.5, nu=0.01, storage=storage, kernel=kernel) as s:
             s.init(rho, u)
             for k in (1, 2, 4):
