@@ -34,8 +34,9 @@ WORKLOAD = dict(workload="D3Q27 decaying isotropic turbulence 256^3 periodic", l
                 nx=256, ny=256, nz=256, stretch=[1.0, 1.0, 1.0], T=1.0 / 3.0, nu=0.0233,
                 u_rms=0.08, k0=4.0, seed=0)
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_NAMES = {0: "automatic", 1: "two-pass", 2: "pipelined", 3: "single-pass"}
-KERNEL_LAUNCHES = {0: "automatic", 1: "k_anomaly+k_collide", 2: "k_pipelined", 3: "k_single_pass"}
+KERNEL_NAMES = {0: "two-pass", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
+KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range",
+                   3: "k_single_pass_fast"}
 # ncu DRAM bytes (read + write) per node update of the pipelined kernel,
 # keyed by the hash of the kernel sources they were measured on.
 MEASURED_TRAFFIC = {}
@@ -201,7 +202,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
     ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="0 automatic, 1 two-pass in place, 2 pipelined in place, 3 single pass (two arrays)")
+                    help="0 automatic, 1 two-pass in place, 2 graph-pipelined in place, 3 single pass (two arrays)")
     ap.add_argument("--reduce-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")

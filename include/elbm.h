@@ -70,14 +70,14 @@ extern "C" {
  *   1 = product-form equilibrium without the correction (Eq. 27eq);
  *   2 = product form truncated to second order in u (Sec. III preamble). */
 #define ELBM_OPT_EQUILIBRIUM 1
-/* ELBM_OPT_KERNEL: 0 = automatic; 1 = two-pass (anomaly pass, collide pass);
- *   2 = pipelined pass (same arithmetic; one cooperative launch per step whose
- *   warps interleave the two phases chunk by chunk, so that the collide phase
- *   re-reads the populations from L2);
- *   3 = single pass with a second population array (D3Q27; each block
- *   recomputes the anomaly around its tile, populations are read once);
- *   4 = graph-pipelined passes (a CUDA graph of per-chunk anomaly and collide
- *   kernels, so that the collide kernels re-read the populations from L2). */
+/* ELBM_OPT_KERNEL: the form of the step; every form evaluates the same per-node
+ *   arithmetic and gives bit-identical results.
+ *   0 = automatic (the two-pass form);
+ *   1 = two-pass, in place: an anomaly pass over the grid, then the collide pass;
+ *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide
+ *       kernels, so that the collide kernels re-read populations from L2;
+ *   3 = single pass with a second population array (D3Q27 only): every block
+ *       recomputes the anomaly around its tile and reads the populations once. */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3

@@ -28,8 +28,6 @@ int cuda_fail(cudaError_t e, const char* what)
                 cudaGetErrorString(e));
 }
 
-constexpr int kStepsPerLaunch = 256;  // bound on the duration of one pipelined launch
-
 }  // namespace
 
 namespace elbm {
@@ -77,7 +75,6 @@ void fill_params(const Solver& s, StepParams& p)
     std::memset(&p, 0, sizeof p);
     p.f = s.f;
     p.q = s.q;
-    p.sync = s.sync;
     p.status = s.status;
     p.nx = s.nx;
     p.ny = s.ny;
@@ -122,34 +119,6 @@ void fill_params(const Solver& s, StepParams& p)
     p.parity = s.parity;
 }
 
-// Order of the phases of one pipelined step, as (type, chunk) pairs
-// (type 0 = anomaly phase, 1 = collide phase): anomaly phases of the last
-// chunk and of chunks 0..L first, then every collide phase followed by the next
-// anomaly phase.  With L >= 1 every phase a collide phase waits for is issued
-// before it (the deadlock-freedom argument of the pipelined kernel).
-static void phase_order(int K, int L, unsigned* out)
-{
-    int n = 0;
-    auto put = [&](int type, int c) {
-        out[2 * n] = (unsigned)type;
-        out[2 * n + 1] = (unsigned)c;
-        ++n;
-    };
-    if (K == 1) {
-        put(0, 0);
-        put(1, 0);
-        return;
-    }
-    put(0, K - 1);
-    const int pro = std::min(L, K - 2);
-    for (int c = 0; c <= pro; ++c) put(0, c);
-    int next_a = pro + 1;
-    for (int j = 0; j < K; ++j) {
-        put(1, j);
-        if (next_a <= K - 2) put(0, next_a++);
-    }
-}
-
 }  // namespace elbm
 
 using elbm::Solver;
@@ -172,8 +141,6 @@ int check_status(elbm_solver* s)
     return ELBM_OK;
 }
 
-bool pipelined_usable(const elbm_solver* s) { return s->pipe.grid > 0 && s->sync != nullptr; }
-
 bool shifted_storage_mode(int storage) { return storage != ELBM_F32; }
 
 // The graph-pipelined step bakes the parameter block into its kernel nodes;
@@ -186,13 +153,8 @@ void drop_graphs(elbm_solver* s)
     }
 }
 
-// Kernel form a step uses: 0 (automatic) means the single-pass form for
-// D3Q27 and the two-pass form for D2Q9.
-int effective_kernel(const elbm_solver* s)
-{
-    if (s->kernel != 0) return s->kernel;
-    return s->D == 3 ? 3 : 1;
-}
+// Kernel form a step uses: 0 (automatic) means the two-pass form.
+int effective_kernel(const elbm_solver* s) { return s->kernel != 0 ? s->kernel : 1; }
 
 size_t population_bytes(const elbm_solver* s)
 {
@@ -204,7 +166,7 @@ size_t population_bytes(const elbm_solver* s)
 // The single-pass form needs a second population array.
 int ensure_second_array(elbm_solver* s, int kernel)
 {
-    const int k = kernel != 0 ? kernel : (s->D == 3 ? 3 : 1);
+    const int k = kernel != 0 ? kernel : 1;
     if (k != 3 || s->f2) return ELBM_OK;
     cudaError_t e = cudaMalloc(&s->f2, population_bytes(s));
     if (e != cudaSuccess) {
@@ -270,22 +232,12 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
     if (e == cudaSuccess) e = cudaMalloc((void**)&s->status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_red, ELBM_NRED * sizeof(double));
-    if (e == cudaSuccess) {
-        s->pipe = (D == 2) ? elbm::pipelined_geometry_impl<2>(*s) : elbm::pipelined_geometry_impl<3>(*s);
-        if (s->pipe.grid > 0) {
-            std::vector<unsigned> words(s->pipe.sync_words, 0u);
-            elbm::phase_order(s->pipe.nchunks, s->pipe.lookahead, words.data() + 2 + 2 * s->pipe.nchunks);
-            e = cudaMalloc((void**)&s->sync, words.size() * sizeof(unsigned));
-            if (e == cudaSuccess)
-                e = cudaMemcpy(s->sync, words.data(), words.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
-        }
-    }
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "elbm_create");
         elbm_destroy(s);
         return rc;
     }
-    s->bytes = population_bytes(s) + qbytes + s->pipe.sync_words * sizeof(unsigned);
+    s->bytes = population_bytes(s) + qbytes;
     const int rc = ensure_second_array(s, s->kernel);
     if (rc != ELBM_OK) {
         elbm_destroy(s);
@@ -303,7 +255,6 @@ void elbm_destroy(elbm_solver* s)
     cudaFree(s->f);
     cudaFree(s->f2);
     cudaFree(s->q);
-    cudaFree(s->sync);
     cudaFree(s->status);
     cudaFree(s->mom);
     cudaFree(s->partials);
@@ -322,9 +273,8 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             s->eq_mode = (int)value;
             return ELBM_OK;
         case ELBM_OPT_KERNEL: {
-            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != 4.0)
-                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2, 3 or 4");
-            if (value == 2.0 && !pipelined_usable(s)) return fail(ELBM_ERR_ARG, "pipelined kernel unavailable");
+            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2 or 3");
             if (value == 3.0 && s->D != 3) return fail(ELBM_ERR_ARG, "the single-pass kernel is D3Q27 only");
             const int rc = ensure_second_array(s, (int)value);
             if (rc != ELBM_OK) return rc;
@@ -440,7 +390,7 @@ int elbm_step(elbm_solver* s, int n)
             e = elbm::step_single_impl<3>(*s, s->f2, &s->launches);
             std::swap(s->f, s->f2);
             --left;
-        } else if (kernel == 4) {
+        } else if (kernel == 2) {
             if (!s->graph_exec[s->parity]) {
                 e = (s->D == 2) ? elbm::build_step_graph_impl<2>(*s, s->parity, &s->graph_exec[s->parity], &s->graph_nodes)
                                 : elbm::build_step_graph_impl<3>(*s, s->parity, &s->graph_exec[s->parity], &s->graph_nodes);
@@ -450,12 +400,6 @@ int elbm_step(elbm_solver* s, int n)
             s->launches += s->graph_nodes;
             s->parity ^= 1;
             --left;
-        } else if (kernel == 2 && pipelined_usable(s)) {
-            const int k = std::min(left, kStepsPerLaunch);
-            e = (s->D == 2) ? elbm::step_pipelined_impl<2>(*s, s->parity, k, &s->launches)
-                            : elbm::step_pipelined_impl<3>(*s, s->parity, k, &s->launches);
-            s->parity = (s->parity + k) & 1;
-            left -= k;
         } else {
             // two-pass (also brings an odd-parity state back to the own-location layout)
             e = (s->D == 2) ? elbm::step_two_pass_impl<2>(*s, s->parity, &s->launches)

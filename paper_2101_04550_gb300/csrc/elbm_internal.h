@@ -17,8 +17,7 @@ constexpr int kMaxQ = 27;
 struct StepParams {
     void* f;              // populations, storage type per `storage`, layout f[i][cell]
     float* q;             // diagonal anomaly field q[a][cell] (Eq. Deviation)
-    unsigned int* sync;   // pipelined kernel: ticket + per-chunk completion counters
-    int* status;          // device status word (bounded waits report here)
+    int* status;          // device status word
     int nx, ny, nz;       // nodes per axis (nz = 1 for D2Q9)
     int N;                // nx*ny*nz
     int plane;            // nx*ny
@@ -43,24 +42,6 @@ struct StepParams {
     int forced;           // g != 0
     int eq_mode;          // 0 extended, 1 product form, 2 second order
     int parity;           // AA streaming parity of the step about to run (0 even, 1 odd)
-    // pipelined kernel geometry
-    int chunk_planes;     // z planes per chunk
-    int nchunks;          // number of z chunks
-    int tile_cells;       // cells per tile
-    int tiles_per_chunk;  // tiles in one phase of one chunk
-    int nsteps;           // steps advanced by one launch
-    int lookahead;        // anomaly phases issued ahead of collide phases
-};
-
-// Chunking of the pipelined step (see pipelined.cuh).
-struct PipeGeom {
-    int grid = 0;            // resident blocks launched
-    int chunk_planes = 0;    // layers (z planes, or y rows for D2Q9) per chunk
-    int nchunks = 0;
-    int tile_cells = 0;
-    int tiles_per_chunk = 0;
-    int lookahead = 0;
-    size_t sync_words = 0;
 };
 
 struct Solver {
@@ -74,7 +55,7 @@ struct Solver {
     double u_ref[3] = {0, 0, 0};   // storage baseline velocity U0 (shifted storage modes)
     int u_ref_auto = 0;            // 1: U0 = mean velocity of the field given to elbm_init
     int eq_mode = 0;
-    int kernel = 0;       // 0 auto, 1 two-pass, 2 pipelined, 3 single pass (two arrays), 4 graph-pipelined
+    int kernel = 0;       // 0 auto, 1 two-pass, 2 graph-pipelined, 3 single pass (two arrays)
     int walls_y = 0;
     int parity = 0;
     int initialised = 0;
@@ -84,8 +65,6 @@ struct Solver {
     void* f = nullptr;                // populations (current)
     void* f2 = nullptr;               // second population array of the single-pass form
     float* q = nullptr;               // anomaly field
-    unsigned int* sync = nullptr;     // pipelined-kernel ticket, counters, phase order
-    PipeGeom pipe;
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};  // graph-pipelined step per parity
     int graph_nodes = 0;
     int* status = nullptr;            // device status word
@@ -106,10 +85,8 @@ void fill_params(const Solver& s, StepParams& p);
 // kernels_d3q27.cu).  Each returns the CUDA error of its launches and adds the
 // number of kernel launches it issued to *launches.
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
-template <int D> cudaError_t step_pipelined_impl(const Solver&, int, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
-template <int D> PipeGeom pipelined_geometry_impl(const Solver&);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);
 template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, long long*);

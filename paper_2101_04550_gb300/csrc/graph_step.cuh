@@ -22,6 +22,15 @@
 
 #include "step_kernels.cuh"
 
+// Chunks the anomaly kernels may run ahead of the collide kernels, and
+// whether consecutive anomaly kernels are also ordered among themselves.
+#ifndef ELBM_GRAPH_LOOKAHEAD
+#define ELBM_GRAPH_LOOKAHEAD 3
+#endif
+#ifndef ELBM_GRAPH_CHAIN
+#define ELBM_GRAPH_CHAIN 0
+#endif
+
 namespace elbm {
 
 template <int D, int ST, int PAR>
@@ -63,7 +72,7 @@ GraphGeom graph_geometry(const Solver& s)
     g.nlayers = (D == 3) ? s.nz : s.ny;
     g.chunk_layers = std::max(1, std::min(g.nlayers, (262144 + g.layer - 1) / g.layer));
     g.nchunks = (g.nlayers + g.chunk_layers - 1) / g.chunk_layers;
-    g.lookahead = 2;
+    g.lookahead = ELBM_GRAPH_LOOKAHEAD;
     return g;
 }
 
@@ -120,7 +129,7 @@ cudaError_t build_graph_typed(const Solver& s, cudaGraphExec_t* out, int* nodes)
     for (size_t k = 0; k < a_order.size() && e == cudaSuccess; ++k) {
         const int c = a_order[k];
         std::vector<cudaGraphNode_t> deps;
-        if (prev_a) deps.push_back(prev_a);
+        if (prev_a && ELBM_GRAPH_CHAIN) deps.push_back(prev_a);
         const int lag = c - g.lookahead;
         if (c != K - 1 && lag >= 0 && c_done[lag]) deps.push_back(C[lag]);
         e = add(fa, c, deps, &A[c]);

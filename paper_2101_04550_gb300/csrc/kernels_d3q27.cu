@@ -1,15 +1,12 @@
 // Instantiation of the step kernels and their launchers for the D3Q27 lattice.
 #include "step_kernels.cuh"
-#include "pipelined.cuh"
 #include "single_pass.cuh"
 #include "graph_step.cuh"
 
 namespace elbm {
 template cudaError_t step_two_pass_impl<3>(const Solver&, int, long long*);
-template cudaError_t step_pipelined_impl<3>(const Solver&, int, int, long long*);
 template cudaError_t step_single_impl<3>(const Solver&, void*, long long*);
 template cudaError_t build_step_graph_impl<3>(const Solver&, int, cudaGraphExec_t*, int*);
-template PipeGeom pipelined_geometry_impl<3>(const Solver&);
 template cudaError_t init_impl<3>(const Solver&, const void*, const void*, int, long long*);
 template cudaError_t moments_impl<3>(const Solver&, void*, void*, int, long long*);
 template cudaError_t get_populations_impl<3>(const Solver&, void*, int, long long*);
