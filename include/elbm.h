@@ -181,6 +181,33 @@ long long elbm_launch_count(const elbm_solver* s);
 /* Baseline velocity U0 of the shifted storage in use, out[3] (zeros for ELBM_F32). */
 int elbm_get_u_ref(const elbm_solver* s, double* out);
 
+/*
+ * Allocation-free step.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory themselves -- applications
+ * that route every device allocation through their own pool, plugins whose
+ * host framework forbids allocations on its threads, or code that records
+ * CUDA work where cudaMalloc is not allowed.  It creates no solver and calls
+ * no allocating routine; the caller passes the populations and gets them back
+ * advanced.
+ *   f        device pointer to float populations f[Q][nz][ny][nx] (unshifted,
+ *            layout of elbm_get_populations), advanced in place by nsteps
+ *            two-pass steps and left in that same layout.
+ *   lattice, nx, ny, nz, stretch, T, nu: as for elbm_create;
+ *            nx*ny*nz must not exceed 262144 (ELBM_ERR_ARG otherwise).
+ *   stream   cudaStream_t to enqueue on; the call returns once the work is
+ *            enqueued (synchronise the stream before reading f).
+ * The anomaly field lives in a fixed 3 MiB device array that this library
+ * holds on every GPU where it is used, until the process exits.  All calls
+ * on a device share that array, so calls whose work overlaps on the GPU (for
+ * example on two streams) race and give wrong results; serialise them.  The
+ * first call on a device looks up the array's device address (set-up that
+ * must not happen inside a stream capture), so make one call, for example
+ * with nsteps = 0, before capturing.  Errors: ELBM_ERR_ARG,
+ * ELBM_ERR_UNREALIZABLE, ELBM_ERR_CUDA; elbm_last_error() has the message.
+ */
+int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const double* stretch, double T,
+                      double nu, float* f, int nsteps, void* stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* elbm_last_error(void);
 

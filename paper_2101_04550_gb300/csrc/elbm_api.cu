@@ -32,6 +32,12 @@ int cuda_fail(cudaError_t e, const char* what)
 
 namespace elbm {
 
+int set_error(int code, const char* msg)
+{
+    std::snprintf(g_err, sizeof g_err, "%s", msg);
+    return code;
+}
+
 bool base_triplet(double T, double lam, double U0, float out[3], double* u0_eff);
 
 size_t storage_bytes(int storage)

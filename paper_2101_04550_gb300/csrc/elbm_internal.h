@@ -79,6 +79,8 @@ struct Solver {
 };
 
 size_t storage_bytes(int storage);
+// Record the message elbm_last_error() returns on the calling thread; returns code.
+int set_error(int code, const char* msg);
 void fill_params(const Solver& s, StepParams& p);
 
 // Launchers, explicitly instantiated per lattice (kernels_d2q9.cu,
