@@ -322,7 +322,8 @@ def main():
     # ---- variants (same workload, other storage / kernel form) ----------
     variants = {}
     if not args.no_variants and rank == 0:
-        for name, st, ker in (("f16_shift_pipelined", elbm.F16_SHIFT, 2), ("f32_two_pass", elbm.F32_SHIFT, 1)):
+        for name, st, ker in (("f16_shift_two_pass", elbm.F16_SHIFT, 1), ("f16_shift_single_pass", elbm.F16_SHIFT, 3),
+                              ("f32_shift_single_pass", elbm.F32_SHIFT, 3), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2)):
             sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every)
             sv.close()
             nsteps = min(args.steps, 200)
