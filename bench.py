@@ -37,9 +37,11 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {0: "two-pass", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
 KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range",
                    3: "k_single_pass_fast"}
-# ncu DRAM bytes (read + write) per node update of the pipelined kernel,
-# keyed by the hash of the kernel sources they were measured on.
-MEASURED_TRAFFIC = {}
+# ncu DRAM bytes (read + write) of one step of the timed kernel form, keyed by
+# the hash of the kernel sources they were measured on, the storage and the form.
+# 339 B/node measured at 192^3 (profiles/k_anomaly_k_collide_d3q27_hit192_f32.md), scaled
+# to the 256^3 step: 339.1 * 256^3 bytes.
+MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47", "f32s", 1): 5.689e9}
 
 
 def kernel_source_hash() -> str:
