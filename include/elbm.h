@@ -178,6 +178,33 @@ long long elbm_device_bytes(const elbm_solver* s);
 /* Number of kernel launches this solver has issued since creation. */
 long long elbm_launch_count(const elbm_solver* s);
 
+/* ------------------------------------------------------------- batches */
+/*
+ * A batch advances many grids together: members share lattice, storage mode
+ * and stream, and may differ in size, stretch, T and nu.  One batched step is
+ * two launches (anomaly pass and collide pass of the two-pass form, Eqs. LBGK,
+ * Deviation, Paastar1, 27eqext) over all members; every member's result is
+ * bit-identical to stepping it alone.  The batch holds the solvers (it does
+ * not own them) and a device table of their parameters, refreshed at every
+ * elbm_batch_step; destroy the batch before any of its solvers.
+ */
+typedef struct elbm_batch elbm_batch;
+
+int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out);
+
+/* Advance every member by nsteps >= 0 steps, asynchronously on the members'
+ * stream.  The first call times one real step with 128- and one with
+ * 256-thread blocks and keeps the faster (the autotuner); the launch sequence
+ * of the remaining steps is captured once as a CUDA graph and replayed while
+ * nsteps stays the same. */
+int elbm_batch_step(elbm_batch* b, int nsteps);
+
+/* Chosen block size (0 before tuning), the two tuning step times in ms
+ * (128, 256) and the number of kernel launches issued so far. */
+int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long long* launches);
+
+void elbm_batch_destroy(elbm_batch* b);
+
 /* Baseline velocity U0 of the shifted storage in use, out[3] (zeros for ELBM_F32). */
 int elbm_get_u_ref(const elbm_solver* s, double* out);
 

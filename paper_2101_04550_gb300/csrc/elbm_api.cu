@@ -129,8 +129,6 @@ void fill_params(const Solver& s, StepParams& p)
 
 using elbm::Solver;
 
-struct elbm_solver : public Solver {};
-
 namespace {
 
 int check_status(elbm_solver* s)

@@ -78,6 +78,13 @@ struct Solver {
     size_t bytes = 0;
 };
 
+// One member of a batch (see batch.cuh).
+struct BatchMember {
+    StepParams p;         // the member's parameter block (its parity field is ignored)
+    int block_begin[2];   // first block of the member in launches of 128 and of 256 threads
+    int parity;           // streaming parity before the first step of a launch sequence
+};
+
 size_t storage_bytes(int storage);
 // Record the message elbm_last_error() returns on the calling thread; returns code.
 int set_error(int code, const char* msg);
@@ -95,5 +102,9 @@ template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, lon
 template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
+template <int D> cudaError_t batch_enqueue_impl(int, int, const BatchMember*, int, int, int, cudaStream_t, long long*);
 
 }  // namespace elbm
+
+// The opaque handle of the C ABI is the solver itself.
+struct elbm_solver : public elbm::Solver {};

@@ -113,12 +113,12 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
 
 // The per-node update once the anomaly field of this time level is complete:
 // gather the post-streaming populations into the thread's shared-memory
-// column `col` (stride kBlock), central difference of q along each axis
+// column `col` (stride STRIDE, the block size), central difference of q along each axis
 // (Eq. Paastar1), extended equilibrium, relaxation, write-back in place.
 // Populations are read back from the stage instead of being held in
 // registers, which keeps the register count low enough for 32 resident
 // warps per SM.
-template <int D, int ST, int PAR>
+template <int D, int ST, int PAR, int STRIDE = kBlock>
 __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, unsigned* col)
 {
     constexpr int Q = Lat<D>::Q;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, un
     for (int i = 0; i < Q; ++i) {
         const int idx = read_slot<D>(n, p.N, i, PAR);
         halves |= (unsigned)(idx & 1) << i;
-        cp_async4(col + i * kBlock, stage_src<ST>(p, idx));
+        cp_async4(col + i * STRIDE, stage_src<ST>(p, idx));
     }
     float d[3] = {0.f, 0.f, 0.f};
     if (p.eq_mode == 0) {
@@ -139,7 +139,7 @@ __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, un
         if (D == 3) d[2] = (q[2 * p.N + n.at(0, 0, 1)] - q[2 * p.N + n.at(0, 0, -1)]) * p.inv_2lam[2];
     }
     cp_async_wait_all();
-    auto gval = [&](int i) { return stage_value<ST>(p, ld_stage(col + i * kBlock), (int)((halves >> i) & 1u), i); };
+    auto gval = [&](int i) { return stage_value<ST>(p, ld_stage(col + i * STRIDE), (int)((halves >> i) & 1u), i); };
     float drho, j[3];
     moments_of<D>(p, gval, drho, j);
     typename S::T* f = static_cast<typename S::T*>(p.f);

@@ -34,7 +34,8 @@ _lib = None
 EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_step", "elbm_moments",
            "elbm_get_populations", "elbm_set_populations", "elbm_reduce", "elbm_sync", "elbm_cells",
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
-           "elbm_last_error"]
+           "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
+           "elbm_step_noalloc"]
 
 
 class ElbmError(RuntimeError):
@@ -77,6 +78,11 @@ def load(build_if_missing: bool = True):
         L.elbm_omega.argtypes = [vp]
         L.elbm_omega.restype = dp
         L.elbm_get_u_ref.argtypes = [vp, ctypes.POINTER(dp)]
+        L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+        L.elbm_batch_step.argtypes = [vp, ip]
+        L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
+        L.elbm_batch_destroy.argtypes = [vp]
+        L.elbm_batch_destroy.restype = None
         L.elbm_last_error.argtypes = []
         L.elbm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -243,6 +249,46 @@ class Solver:
     @property
     def handle(self):
         return self._h
+
+
+class Batch:
+    """Solvers of one lattice, storage mode and stream advanced together (two
+    launches per step for the whole batch, replayed from a CUDA graph)."""
+
+    def __init__(self, solvers):
+        L = load()
+        self.solvers = list(solvers)  # the batch refers to them; keep them alive
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        _check(L.elbm_batch_create(arr, len(self.solvers), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n=1):
+        _check(load().elbm_batch_step(self._h, int(n)))
+
+    def info(self):
+        bs = ctypes.c_int()
+        ms = (ctypes.c_double * 2)()
+        launches = ctypes.c_longlong()
+        _check(load().elbm_batch_info(self._h, ctypes.byref(bs), ms, ctypes.byref(launches)))
+        return {"block_size": bs.value, "tuned_ms": {128: ms[0], 256: ms[1]}, "launches": launches.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().elbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def _addr(b):

@@ -1,0 +1,218 @@
+"""Serving loop: continuous batching of independent lattice Boltzmann solves.
+
+Requests (a grid, its stretch, temperature, viscosity, advection velocity,
+storage mode and number of steps) arrive over time.  The server keeps the
+populations of admitted requests resident on the GPU, admits waiting
+requests whenever the HBM budget and the slot limit allow, and advances all
+resident solves together in chunks of steps with the batched step of the
+library (one CUDA graph of two launches per step for every group of requests
+that share lattice and storage mode).  Requests that arrive while others run
+join at the next chunk boundary; finished ones are read out and freed.  The
+"plain" mode serves the same trace one request at a time in arrival order,
+with per-step launches and no graphs.
+
+Every computation runs in the CUDA library; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import elbm, inputs
+
+Q_BYTES = {elbm.F32: 4, elbm.F32_SHIFT: 4, elbm.F16_SHIFT: 2, elbm.BF16_SHIFT: 2}
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the trace
+    n: tuple                       # (nx, ny, nz)
+    stretch: tuple                 # (lam_x, lam_y, lam_z)
+    T: float
+    nu: float
+    advection: tuple               # uniform velocity added to the initial field
+    storage: int
+    steps: int
+    kind: str                      # "shear" or "taylor_green"
+    seed: int
+    lattice: int = elbm.D3Q27
+
+    @property
+    def cells(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def device_bytes(self) -> int:
+        """Populations (with tail padding) and the anomaly field."""
+        return self.lattice * self.cells * Q_BYTES[self.storage] + 16 + 3 * self.cells * 4
+
+
+def make_trace(n_requests=200, rate=20.0, seed=0, steps=2000, sizes=(32, 48, 64, 96, 128)):
+    """Seeded Poisson trace: sizes uniform in sizes^3 and 64x32x64 with stretch
+    (1, 2, 1); T uniform in [1/3, 0.6]; advection speed uniform in [0, 0.3]
+    along a random direction; nu chosen so that omega is uniform in
+    [1.6, 1.95]; storage FP32 or FP16 (shifted) with equal odds."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    shapes = [((s, s, s), (1.0, 1.0, 1.0)) for s in sizes] + [((64, 32, 64), (1.0, 2.0, 1.0))]
+    for rid in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        n, lam = shapes[rng.integers(len(shapes))]
+        T = rng.uniform(1.0 / 3.0, 0.6)
+        omega = rng.uniform(1.6, 1.95)
+        nu = (1.0 / omega - 0.5) * T
+        speed = rng.uniform(0.0, 0.3)
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        storage = elbm.F32_SHIFT if rng.random() < 0.5 else elbm.F16_SHIFT
+        kind = "shear" if rng.random() < 0.5 else "taylor_green"
+        out.append(Request(rid, t, n, lam, float(T), float(nu), tuple(float(v) for v in speed * d),
+                           storage, steps, kind, int(rng.integers(1 << 30))))
+    return out
+
+
+def initial_field(req: Request):
+    """Initial rho, u of a request (shear wave along a seeded lattice direction,
+    or a Taylor-Green vortex), plus its uniform advection."""
+    rng = np.random.Generator(np.random.PCG64(req.seed))
+    if req.kind == "shear":
+        kd = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1)][rng.integers(6)]
+        k = np.array(kd, float)
+        s_dir = np.cross(k, rng.standard_normal(3))
+        rho, u, _, _ = inputs.shear_wave(req.n, req.stretch, kd, tuple(s_dir), 1e-2, 0.0)
+    else:
+        rho, u = inputs.taylor_green_3d(req.n, req.stretch, U=0.02)
+    for a in range(3):
+        u[a] += req.advection[a]
+    return rho, u
+
+
+class Server:
+    """Continuous-batching server over one GPU stream.
+
+    hbm_budget   bytes of populations + anomaly fields that may be resident
+    chunk_steps  steps between admission points
+    max_active   resident requests at most
+    clock        callable giving seconds (wall clock by default)
+    """
+
+    def __init__(self, hbm_budget=8 << 30, chunk_steps=100, max_active=64, clock=time.perf_counter,
+                 stream=None, sleep=time.sleep):
+        self.hbm_budget = int(hbm_budget)
+        self.chunk_steps = int(chunk_steps)
+        self.max_active = int(max_active)
+        self.clock = clock
+        self.sleep = sleep
+        self.stream = stream
+        self.results = {}
+        self.failed = {}
+
+    def _start(self, req):
+        s = elbm.Solver(req.lattice, req.n, stretch=req.stretch, T=req.T, nu=req.nu, storage=req.storage,
+                        stream=self.stream, kernel=1,
+                        u_ref=req.advection if req.storage != elbm.F32 else None)
+        rho, u = initial_field(req)
+        s.init(rho, u)
+        return s
+
+    def _finish(self, req, solver, t_start, t_admit):
+        _, u = solver.moments(dtype=np.float32)
+        t_done = self.clock() - t_start
+        solver.close()
+        self.results[req.rid] = {"u": u, "arrival": req.arrival, "admitted": t_admit, "done": t_done,
+                                 "latency": t_done - req.arrival, "cells": req.cells, "steps": req.steps}
+
+    def run(self, trace, mode="batched"):
+        """Serve a trace; returns the summary (latencies, makespan, throughput)."""
+        self.results = {}
+        self.failed = {}
+        trace = sorted(trace, key=lambda r: r.arrival)
+        t0 = self.clock()
+        if mode == "plain":
+            for req in trace:
+                now = self.clock() - t0
+                if now < req.arrival:
+                    self.sleep(req.arrival - now)
+                t_admit = self.clock() - t0
+                s = self._start(req)
+                s.step(req.steps)
+                self._finish(req, s, t0, t_admit)
+            return self.summary(trace)
+
+        pending = collections.deque(trace)
+        queue = collections.deque()
+        active = []           # [req, solver, steps_left, t_admit]
+        used = 0
+        batches = {}          # group key -> (member ids, Batch)
+        while pending or queue or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.popleft())
+            while queue and len(active) < self.max_active and used + queue[0].device_bytes() <= self.hbm_budget:
+                req = queue[0]
+                try:
+                    solver = self._start(req)
+                except elbm.ElbmError as err:
+                    if err.code != -3 or not active:  # out of memory with nothing to wait for: give up on it
+                        queue.popleft()
+                        self.failed[req.rid] = str(err)
+                    break  # out of memory while others run: retry once some finish
+                queue.popleft()
+                used += req.device_bytes()
+                active.append([req, solver, req.steps, self.clock() - t0])
+            if not active:
+                if queue and used + queue[0].device_bytes() > self.hbm_budget:
+                    req = queue.popleft()  # larger than the whole budget
+                    self.failed[req.rid] = f"needs {req.device_bytes()} bytes, budget {self.hbm_budget}"
+                    continue
+                if pending and not queue:
+                    self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
+                continue
+            chunk = min(self.chunk_steps, min(a[2] for a in active))
+            groups = collections.defaultdict(list)
+            for a in active:
+                groups[(a[0].lattice, a[0].storage)].append(a)
+            for key, members in groups.items():
+                ids = tuple(a[0].rid for a in members)
+                if key not in batches or batches[key][0] != ids:
+                    if key in batches:
+                        batches[key][1].close()
+                    batches[key] = (ids, elbm.Batch([a[1] for a in members]))
+                batches[key][1].step(chunk)
+            for key in list(batches):
+                if key not in groups:
+                    batches.pop(key)[1].close()
+            still = []
+            for a in active:
+                a[2] -= chunk
+                if a[2] == 0:
+                    for key, (ids, b) in list(batches.items()):
+                        if a[0].rid in ids:
+                            b.close()
+                            batches.pop(key)
+                    self._finish(a[0], a[1], t0, a[3])
+                    used -= a[0].device_bytes()
+                else:
+                    still.append(a)
+            active = still
+        for _, b in batches.values():
+            b.close()
+        return self.summary(trace)
+
+    def summary(self, trace):
+        served = [r for r in trace if r.rid in self.results]
+        lat = np.array([self.results[r.rid]["latency"] for r in served]) if served else np.array([np.nan])
+        first = min(r.arrival for r in trace)
+        makespan = max(self.results[r.rid]["done"] for r in served) - first if served else float("nan")
+        work = sum(r.cells * r.steps for r in served)
+        span = max(r.arrival for r in trace) - first
+        offered = sum(r.cells * r.steps for r in trace) / span / 1e6 if span > 0 else float("nan")
+        return {"requests": len(trace), "served": len(served), "failed": len(self.failed),
+                "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+                "makespan_s": float(makespan), "aggregate_MLUPS": work / makespan / 1e6,
+                "offered_MLUPS": offered, "node_updates": int(work)}

@@ -1,0 +1,77 @@
+"""Batched step: grids of different sizes, stretches, temperatures and
+viscosities advanced together give bit for bit the states of stepping each
+alone (the per-node arithmetic is the same), also for members that join at
+the other streaming parity and that are stepped alone afterwards."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2101_04550_gb300 import elbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    elbm.load()
+
+
+SPECS3 = [((32, 32, 32), (1.0, 1.0, 1.0), 1 / 3, 0.02), ((48, 40, 36), (1.0, 2.0, 1.0), 0.5, 0.01),
+          ((20, 12, 9), (1.5, 1.0, 2.0), 0.45, 0.05), ((64, 32, 64), (1.0, 2.0, 1.0), 0.6, 0.015)]
+SPECS2 = [((64, 64, 1), (1.0, 1.0, 1.0), 1 / 3, 0.02), ((100, 37, 1), (2.0, 1.0, 1.0), 0.5, 0.03)]
+
+
+def _fields(n, seed, D):
+    if D == 3:
+        return inputs.isotropic_turbulence(n, seed=seed, k0=3.0, u_rms=0.05)
+    rho, u = inputs.double_shear_layer(n[:2], U=0.08)
+    return rho, u
+
+
+def _make(lattice, spec, storage, seed):
+    n, lam, T, nu = spec
+    D = 3 if lattice == elbm.D3Q27 else 2
+    s = elbm.Solver(lattice, n, stretch=lam, T=T, nu=nu, storage=storage, kernel=1,
+                    stream=torch.cuda.current_stream())
+    rho, u = _fields(n, seed, D)
+    s.init(rho, u)
+    return s
+
+
+@pytest.mark.parametrize("lattice,specs", [(elbm.D3Q27, SPECS3), (elbm.D2Q9, SPECS2)])
+@pytest.mark.parametrize("storage", [elbm.F32_SHIFT, elbm.F16_SHIFT])
+def test_batch_matches_solo_bitwise(lattice, specs, storage):
+    solo = [_make(lattice, sp, storage, k) for k, sp in enumerate(specs)]
+    mixed = [_make(lattice, sp, storage, k) for k, sp in enumerate(specs)]
+    # one member joins at the odd parity
+    solo[1].step(1)
+    mixed[1].step(1)
+    for s in solo:
+        s.step(23)
+    with elbm.Batch(mixed) as b:
+        b.step(3)      # two tuning steps, then one replayed step
+        b.step(10)     # captured sequence of 10 steps
+        b.step(10)     # replay
+        info = b.info()
+    assert info["block_size"] in (128, 256)
+    for s, m in zip(solo, mixed):
+        assert m.steps_done == s.steps_done
+        assert np.array_equal(s.get_populations(), m.get_populations())
+    # members keep stepping alone after the batch is gone
+    for s, m in zip(solo, mixed):
+        s.step(3)
+        m.step(3)
+        assert np.array_equal(s.get_populations(), m.get_populations())
+    for s in solo + mixed:
+        s.close()
+
+
+def test_batch_rejects_mixed_storage():
+    a = _make(elbm.D3Q27, SPECS3[0], elbm.F32_SHIFT, 0)
+    b = _make(elbm.D3Q27, SPECS3[2], elbm.F16_SHIFT, 1)
+    with pytest.raises(elbm.ElbmError):
+        elbm.Batch([a, b])
+    a.close()
+    b.close()

@@ -254,3 +254,16 @@ def test_mass_momentum_conserved_on_gpu():
     assert abs(r1["mass"] - r0["mass"]) / r0["mass"] < 1e-6
     for k in ("mom_x", "mom_y", "mom_z"):
         assert abs(r1[k] - r0[k]) / r0["mass"] < 1e-7
+
+
+def test_full_size_benchmark_workload_two_steps():
+    """The benchmark workload at full size (D3Q27 256^3 turbulence, T = 1/3,
+    nu = 0.0233, FP32-shift storage), in the launch configurations bench.py
+    times, against the oracle on every node after two steps (both parities);
+    FP16 storage and the single-pass form on the same field."""
+    n = (256, 256, 256)
+    rho, u = inputs.isotropic_turbulence(n, seed=0, k0=4.0, u_rms=0.08)
+    _, uo = run_oracle(3, n, (1.0, 1.0, 1.0), 1 / 3, 0.0233, rho, u, 2)
+    for storage, kernel, tol in ((elbm.F32_SHIFT, 1, 1e-5), (elbm.F32_SHIFT, 3, 1e-5), (elbm.F16_SHIFT, 1, 2e-3)):
+        _, ug = run_gpu(elbm.D3Q27, n, (1.0, 1.0, 1.0), 1 / 3, 0.0233, rho, u, 2, storage, kernel)
+        assert rel_linf(ug, uo) <= tol, (storage, kernel)
