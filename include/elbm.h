@@ -192,11 +192,20 @@ typedef struct elbm_batch elbm_batch;
 
 int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out);
 
-/* Advance every member by nsteps >= 0 steps, asynchronously on the members'
- * stream.  The first call times one real step with 128- and one with
- * 256-thread blocks and keeps the faster (the autotuner); the launch sequence
- * of the remaining steps is captured once as a CUDA graph and replayed while
- * nsteps stays the same. */
+/* Membership: a solver joins (same lattice, storage mode and stream as the
+ * batch, initialised, not yet a member) or leaves between elbm_batch_step
+ * calls; joining and leaving need no new CUDA graph unless the batch grows
+ * beyond twice its earlier block count.  elbm_batch_size gives the member count. */
+int elbm_batch_add(elbm_batch* b, elbm_solver* s);
+int elbm_batch_remove(elbm_batch* b, elbm_solver* s);
+int elbm_batch_size(const elbm_batch* b);
+
+/* Advance every member by nsteps >= 0 steps, asynchronously with respect to
+ * the device, ordered after earlier work on the members' stream.  The first
+ * batch of a (lattice, storage) kind in the process times one real step with
+ * 128- and one with 256-thread blocks and keeps the faster for every later
+ * batch of that kind (the autotuner); the launch sequence of nsteps steps is
+ * captured once as a CUDA graph, on a stream of the batch's own, and replayed. */
 int elbm_batch_step(elbm_batch* b, int nsteps);
 
 /* Chosen block size (0 before tuning), the two tuning step times in ms

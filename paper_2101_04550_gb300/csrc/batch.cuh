@@ -27,10 +27,15 @@ __device__ __forceinline__ int batch_member_of(const BatchMember* m, int nm, int
     return lo;
 }
 
-// The owning member's parameter block, copied to shared memory by thread 0.
+// The owning member's parameter block, copied to shared memory; -1 for the
+// blocks beyond the batch's current total (launches are sized for the
+// batch's capacity, so that membership changes need no new launch sequence).
 template <int BS>
-__device__ __forceinline__ int batch_prologue(const BatchMember* members, int nm, StepParams& sp, int& parity)
+__device__ __forceinline__ int batch_prologue(const BatchHeader* h, StepParams& sp, int& parity)
 {
+    if ((int)blockIdx.x >= h->blocks[BS == 128 ? 0 : 1]) return -1;
+    const BatchMember* members = h->members;
+    const int nm = h->count;
     __shared__ int s_member;
     if (threadIdx.x == 0) s_member = batch_member_of<BS>(members, nm, blockIdx.x);
     __syncthreads();
@@ -44,12 +49,12 @@ __device__ __forceinline__ int batch_prologue(const BatchMember* members, int nm
 }
 
 template <int D, int ST, int BS>
-__global__ void __launch_bounds__(BS) k_batch_anomaly(const BatchMember* members, int nm, int step)
+__global__ void __launch_bounds__(BS) k_batch_anomaly(const BatchHeader* h, int step)
 {
     __shared__ StepParams sp;
     int parity0;
-    const int cell = batch_prologue<BS>(members, nm, sp, parity0);
-    if (cell >= sp.N || sp.eq_mode != 0) return;
+    const int cell = batch_prologue<BS>(h, sp, parity0);
+    if (cell < 0 || cell >= sp.N || sp.eq_mode != 0) return;
     const Node n = make_node<D>(sp, cell);
     float g[Lat<D>::Q];
     if (((parity0 + step) & 1) == 0) gather<D, ST, 0>(sp, n, g);
@@ -62,31 +67,32 @@ __global__ void __launch_bounds__(BS) k_batch_anomaly(const BatchMember* members
 }
 
 template <int D, int ST, int BS>
-__global__ void __launch_bounds__(BS, 4 * kBlock / BS) k_batch_collide(const BatchMember* members, int nm, int step)
+__global__ void __launch_bounds__(BS, 4 * kBlock / BS) k_batch_collide(const BatchHeader* h, int step)
 {
     __shared__ StepParams sp;
     __shared__ unsigned stage[Lat<D>::Q * BS];
     int parity0;
-    const int cell = batch_prologue<BS>(members, nm, sp, parity0);
-    if (cell >= sp.N) return;
+    const int cell = batch_prologue<BS>(h, sp, parity0);
+    if (cell < 0 || cell >= sp.N) return;
     if (((parity0 + step) & 1) == 0) collide_staged<D, ST, 0, BS>(sp, cell, stage + threadIdx.x);
     else collide_staged<D, ST, 1, BS>(sp, cell, stage + threadIdx.x);
 }
 
 // Enqueue `nsteps` batched steps on `stream`: for step k, the anomaly pass and
-// the collide pass over every member (block size BS, `blocks` blocks in total).
+// the collide pass over every member (block size BS, grids of `blocks`
+// blocks, at least the batch's current total).
 template <int D>
-cudaError_t batch_enqueue_impl(int storage, int block_size, const BatchMember* members, int nm, int blocks,
-                               int nsteps, cudaStream_t stream, long long* launches)
+cudaError_t batch_enqueue_impl(int storage, int block_size, const BatchHeader* h, int blocks, int nsteps,
+                               cudaStream_t stream, long long* launches)
 {
     for (int k = 0; k < nsteps; ++k) {
         ELBM_DISPATCH_STORAGE(storage, {
             if (block_size == 128) {
-                k_batch_anomaly<D, ST, 128><<<blocks, 128, 0, stream>>>(members, nm, k);
-                k_batch_collide<D, ST, 128><<<blocks, 128, 0, stream>>>(members, nm, k);
+                k_batch_anomaly<D, ST, 128><<<blocks, 128, 0, stream>>>(h, k);
+                k_batch_collide<D, ST, 128><<<blocks, 128, 0, stream>>>(h, k);
             } else {
-                k_batch_anomaly<D, ST, 256><<<blocks, 256, 0, stream>>>(members, nm, k);
-                k_batch_collide<D, ST, 256><<<blocks, 256, 0, stream>>>(members, nm, k);
+                k_batch_anomaly<D, ST, 256><<<blocks, 256, 0, stream>>>(h, k);
+                k_batch_collide<D, ST, 256><<<blocks, 256, 0, stream>>>(h, k);
             }
         });
         *launches += 2;

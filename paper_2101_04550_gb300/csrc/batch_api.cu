@@ -1,9 +1,17 @@
 // C ABI of the batched step (elbm_batch_*, declared in include/elbm.h):
-// membership checks, the device member table, the block-size autotuner and
-// the CUDA graph of a launch sequence.
+// membership, the device member table, the block-size autotuner and the CUDA
+// graphs of launch sequences.
+//
+// The batched kernels read the member count, the member table and the block
+// totals from device memory, and the launch sequences are sized for the
+// batch's block capacity, so members can join and leave without a new graph:
+// only a capacity increase (or a new block size or step count) captures one.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "elbm_internal.h"
@@ -11,14 +19,18 @@
 struct elbm_batch {
     std::vector<elbm_solver*> members;
     std::vector<elbm::BatchMember> table;
-    elbm::BatchMember* d_table = nullptr;
+    elbm::BatchHeader header{};
+    unsigned char* d_buf = nullptr;    // header, then the member table
+    size_t d_capacity = 0;             // members the device buffer holds
     int lattice = 0, storage = 0, D = 0;
-    int blocks[2] = {0, 0};        // total blocks for 128- and 256-thread launches
-    cudaStream_t stream = nullptr;
-    int block_size = 0;            // 0 until the autotuner has chosen 128 or 256
-    float tuned_ms[2] = {0, 0};    // time of one tuning step per block size
-    cudaGraphExec_t exec = nullptr;
-    int exec_steps = 0;
+    int blocks[2] = {0, 0};            // current block totals (128, 256 threads)
+    int grid[2] = {0, 0};              // block capacity the graphs were captured for
+    cudaStream_t stream = nullptr;      // the members' stream
+    cudaStream_t exec_stream = nullptr; // private stream that captures and replays graphs
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int block_size = 0;                // chosen by the autotuner
+    float tuned_ms[2] = {0, 0};
+    std::map<int, cudaGraphExec_t> graphs;  // by step count, for block_size and grid
     long long launches = 0;
 };
 
@@ -33,24 +45,76 @@ int bcuda(cudaError_t e, const char* what)
     return elbm::set_error(e == cudaErrorMemoryAllocation ? ELBM_ERR_OOM : ELBM_ERR_CUDA, buf);
 }
 
-// Refresh every member's parameter block and parity and upload the table.
-cudaError_t upload_table(elbm_batch* b)
+// Block size chosen by the autotuner, per (lattice, storage), shared by every
+// batch of the process: the first batch of a kind pays the two tuning steps.
+std::mutex g_tune_lock;
+std::map<std::pair<int, int>, int> g_tuned;
+
+void drop_graphs(elbm_batch* b)
 {
-    for (size_t k = 0; k < b->members.size(); ++k) {
-        elbm::fill_params(*b->members[k], b->table[k].p);
-        b->table[k].parity = b->members[k]->parity;
-    }
-    return cudaMemcpyAsync(b->d_table, b->table.data(), b->table.size() * sizeof(elbm::BatchMember),
-                           cudaMemcpyHostToDevice, b->stream);
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
 }
 
-cudaError_t enqueue(elbm_batch* b, int block_size, int nsteps)
+cudaError_t join_in(elbm_batch* b)
 {
-    const int blocks = b->blocks[block_size == 128 ? 0 : 1];
-    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, b->d_table, (int)b->members.size(),
-                                                     blocks, nsteps, b->stream, &b->launches)
-                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, b->d_table, (int)b->members.size(),
-                                                     blocks, nsteps, b->stream, &b->launches);
+    cudaError_t e = cudaEventRecord(b->ev_in, b->stream);
+    return e == cudaSuccess ? cudaStreamWaitEvent(b->exec_stream, b->ev_in, 0) : e;
+}
+cudaError_t join_out(elbm_batch* b)
+{
+    cudaError_t e = cudaEventRecord(b->ev_out, b->exec_stream);
+    return e == cudaSuccess ? cudaStreamWaitEvent(b->stream, b->ev_out, 0) : e;
+}
+
+// Recompute the block layout, refresh every member's parameter block and
+// parity, and upload header and table (on the private stream, ordered before
+// the next launch sequence).
+cudaError_t upload(elbm_batch* b)
+{
+    const size_t n = b->members.size();
+    long long begin128 = 0, begin256 = 0;
+    b->table.resize(n);
+    for (size_t k = 0; k < n; ++k) {
+        elbm_solver* s = b->members[k];
+        elbm::fill_params(*s, b->table[k].p);
+        b->table[k].parity = s->parity;
+        b->table[k].block_begin[0] = (int)begin128;
+        b->table[k].block_begin[1] = (int)begin256;
+        begin128 += (s->N + 127) / 128;
+        begin256 += (s->N + 255) / 256;
+    }
+    b->blocks[0] = (int)begin128;
+    b->blocks[1] = (int)begin256;
+    if (n > b->d_capacity) {
+        const size_t cap = std::max<size_t>(2 * b->d_capacity, std::max<size_t>(n, 8));
+        unsigned char* nb = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&nb, sizeof(elbm::BatchHeader) + cap * sizeof(elbm::BatchMember),
+                                        b->exec_stream);
+        if (e != cudaSuccess) return e;
+        if (b->d_buf) cudaFreeAsync(b->d_buf, b->exec_stream);
+        b->d_buf = nb;
+        b->d_capacity = cap;
+        drop_graphs(b);  // the graphs point at the old buffer
+    }
+    b->header.members = reinterpret_cast<const elbm::BatchMember*>(b->d_buf + sizeof(elbm::BatchHeader));
+    b->header.count = (int)n;
+    b->header.blocks[0] = b->blocks[0];
+    b->header.blocks[1] = b->blocks[1];
+    cudaError_t e = cudaMemcpyAsync(b->d_buf, &b->header, sizeof(b->header), cudaMemcpyHostToDevice, b->exec_stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(b->d_buf + sizeof(elbm::BatchHeader), b->table.data(), n * sizeof(elbm::BatchMember),
+                            cudaMemcpyHostToDevice, b->exec_stream);
+    // (copies from pageable memory return once the source has been read, so
+    // the host table may be rewritten by the next upload)
+    return e;
+}
+
+cudaError_t enqueue(elbm_batch* b, int block_size, int grid, int nsteps)
+{
+    const auto* h = reinterpret_cast<const elbm::BatchHeader*>(b->d_buf);
+    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, h, grid, nsteps, b->exec_stream, &b->launches)
+                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, h, grid, nsteps, b->exec_stream, &b->launches);
 }
 
 void advance_members(elbm_batch* b, int nsteps)
@@ -69,27 +133,45 @@ int autotune(elbm_batch* b, int* steps_left)
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
+    int rc = ELBM_OK;
     for (int c = 0; c < 2 && *steps_left > 0; ++c) {
-        cudaError_t e = upload_table(b);
-        if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
-        if (e == cudaSuccess) e = enqueue(b, candidates[c], 1);
-        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        const int bs = candidates[c], idx = bs == 128 ? 0 : 1;
+        cudaError_t e = join_in(b);
+        if (e == cudaSuccess) e = upload(b);
+        if (e == cudaSuccess) e = cudaEventRecord(t0, b->exec_stream);
+        if (e == cudaSuccess) e = enqueue(b, bs, b->blocks[idx], 1);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->exec_stream);
+        if (e == cudaSuccess) e = join_out(b);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
         if (e != cudaSuccess) {
-            cudaEventDestroy(t0);
-            cudaEventDestroy(t1);
-            return bcuda(e, "elbm_batch_step (tuning)");
+            rc = bcuda(e, "elbm_batch_step (tuning)");
+            break;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, t0, t1);
-        b->tuned_ms[candidates[c] == 128 ? 0 : 1] = ms;
+        b->tuned_ms[idx] = ms;
         advance_members(b, 1);
         --*steps_left;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    if (b->tuned_ms[0] > 0.f && b->tuned_ms[1] > 0.f)
+    if (rc == ELBM_OK && b->tuned_ms[0] > 0.f && b->tuned_ms[1] > 0.f) {
         b->block_size = (b->tuned_ms[0] < b->tuned_ms[1]) ? 128 : 256;
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        g_tuned[{b->lattice, b->storage}] = b->block_size;
+    }
+    return rc;
+}
+
+int check_member(const elbm_batch* b, const elbm_solver* s)
+{
+    if (!s) return bfail(ELBM_ERR_ARG, "NULL solver in batch");
+    if (!s->initialised) return bfail(ELBM_ERR_STATE, "batch member not initialised");
+    if (s->lattice != b->lattice || s->storage != b->storage)
+        return bfail(ELBM_ERR_ARG, "batch members must share lattice and storage mode");
+    if (s->stream != b->stream) return bfail(ELBM_ERR_ARG, "batch members must share one stream");
+    if (std::find(b->members.begin(), b->members.end(), s) != b->members.end())
+        return bfail(ELBM_ERR_ARG, "solver listed twice in batch");
     return ELBM_OK;
 }
 
@@ -97,80 +179,107 @@ int autotune(elbm_batch* b, int* steps_left)
 
 extern "C" {
 
+void elbm_batch_destroy(elbm_batch* b);
+
 int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out)
 {
     if (!out) return bfail(ELBM_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (!solvers || n < 1) return bfail(ELBM_ERR_ARG, "a batch needs at least one solver");
+    if (!solvers || n < 1 || !solvers[0]) return bfail(ELBM_ERR_ARG, "a batch needs at least one solver");
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     elbm_batch* b = new elbm_batch();
-    long long begin128 = 0, begin256 = 0;
+    b->lattice = solvers[0]->lattice;
+    b->storage = solvers[0]->storage;
+    b->D = solvers[0]->D;
+    b->stream = solvers[0]->stream;
     for (int k = 0; k < n; ++k) {
-        elbm_solver* s = solvers[k];
-        if (!s) { delete b; return bfail(ELBM_ERR_ARG, "NULL solver in batch"); }
-        if (!s->initialised) { delete b; return bfail(ELBM_ERR_STATE, "batch member not initialised"); }
-        if (k == 0) {
-            b->lattice = s->lattice;
-            b->storage = s->storage;
-            b->D = s->D;
-            b->stream = s->stream;
-        } else if (s->lattice != b->lattice || s->storage != b->storage) {
+        const int rc = check_member(b, solvers[k]);
+        if (rc != ELBM_OK) {
             delete b;
-            return bfail(ELBM_ERR_ARG, "batch members must share lattice and storage mode");
-        } else if (s->stream != b->stream) {
-            delete b;
-            return bfail(ELBM_ERR_ARG, "batch members must share one stream");
+            return rc;
         }
-        for (int j = 0; j < k; ++j)
-            if (solvers[j] == s) { delete b; return bfail(ELBM_ERR_ARG, "solver listed twice in batch"); }
-        b->members.push_back(s);
-        elbm::BatchMember m{};
-        m.block_begin[0] = (int)begin128;
-        m.block_begin[1] = (int)begin256;
-        begin128 += (s->N + 127) / 128;
-        begin256 += (s->N + 255) / 256;
-        b->table.push_back(m);
+        b->members.push_back(solvers[k]);
     }
-    if (begin128 >= (1ll << 31)) { delete b; return bfail(ELBM_ERR_ARG, "batch too large"); }
-    b->blocks[0] = (int)begin128;
-    b->blocks[1] = (int)begin256;
-    cudaError_t e = cudaMalloc((void**)&b->d_table, b->table.size() * sizeof(elbm::BatchMember));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        auto it = g_tuned.find({b->lattice, b->storage});
+        if (it != g_tuned.end()) b->block_size = it->second;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->exec_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete b;
+        elbm_batch_destroy(b);
         return bcuda(e, "elbm_batch_create");
     }
     *out = b;
     return ELBM_OK;
 }
 
+int elbm_batch_add(elbm_batch* b, elbm_solver* s)
+{
+    if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
+    const int rc = check_member(b, s);
+    if (rc != ELBM_OK) return rc;
+    b->members.push_back(s);
+    return ELBM_OK;
+}
+
+int elbm_batch_remove(elbm_batch* b, elbm_solver* s)
+{
+    if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
+    auto it = std::find(b->members.begin(), b->members.end(), s);
+    if (it == b->members.end()) return bfail(ELBM_ERR_ARG, "solver is not in the batch");
+    b->members.erase(it);
+    return ELBM_OK;
+}
+
+int elbm_batch_size(const elbm_batch* b) { return b ? (int)b->members.size() : 0; }
+
 int elbm_batch_step(elbm_batch* b, int nsteps)
 {
     if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return bfail(ELBM_ERR_ARG, "nsteps must be >= 0");
+    if (b->members.empty() || nsteps == 0) return ELBM_OK;
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     int left = nsteps;
     if (b->block_size == 0) {
         const int rc = autotune(b, &left);
         if (rc != ELBM_OK) return rc;
     }
     if (left == 0) return ELBM_OK;
-    const int bs = b->block_size ? b->block_size : 256;
-    cudaError_t e = upload_table(b);
-    if (e == cudaSuccess && (!b->exec || b->exec_steps != left)) {
-        // capture the launch sequence of `left` steps once and replay it
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            const cudaError_t e1 = enqueue(b, bs, left);
-            e = cudaStreamEndCapture(b->stream, &g);
-            if (e == cudaSuccess) e = e1;
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
-        if (g) cudaGraphDestroy(g);
-        b->exec_steps = (e == cudaSuccess) ? left : 0;
+    const int bs = b->block_size ? b->block_size : 256, idx = bs == 128 ? 0 : 1;
+    cudaError_t e = join_in(b);
+    if (e == cudaSuccess) e = upload(b);
+    if (e == cudaSuccess && b->blocks[idx] > b->grid[idx]) {
+        // capacity: twice the current need, so that joining members rarely recapture
+        b->grid[idx] = std::max(2 * b->blocks[idx], 1);
+        drop_graphs(b);
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
-    if (e != cudaSuccess) return bcuda(e, "elbm_batch_step");
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) {
+        auto it = b->graphs.find(left);
+        if (it != b->graphs.end()) {
+            exec = it->second;
+        } else {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->exec_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = enqueue(b, bs, b->grid[idx], left);
+                e = cudaStreamEndCapture(b->exec_stream, &g);
+                if (e == cudaSuccess) e = e1;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) b->graphs[left] = exec;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->exec_stream);
+    if (e == cudaSuccess) e = join_out(b);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bcuda(e, "elbm_batch_step");
+    }
     advance_members(b, left);
     return ELBM_OK;
 }
@@ -190,9 +299,12 @@ int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long
 void elbm_batch_destroy(elbm_batch* b)
 {
     if (!b) return;
-    cudaStreamSynchronize(b->stream);
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    cudaFree(b->d_table);
+    if (b->exec_stream) cudaStreamSynchronize(b->exec_stream);
+    drop_graphs(b);
+    if (b->d_buf) cudaFree(b->d_buf);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->exec_stream) cudaStreamDestroy(b->exec_stream);
     delete b;
 }
 

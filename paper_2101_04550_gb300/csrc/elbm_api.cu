@@ -172,7 +172,7 @@ int ensure_second_array(elbm_solver* s, int kernel)
 {
     const int k = kernel != 0 ? kernel : 1;
     if (k != 3 || s->f2) return ELBM_OK;
-    cudaError_t e = cudaMalloc(&s->f2, population_bytes(s));
+    cudaError_t e = cudaMallocAsync(&s->f2, population_bytes(s), s->stream);
     if (e != cudaSuccess) {
         s->f2 = nullptr;
         return cuda_fail(e, "second population array");
@@ -231,11 +231,11 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     const size_t qbytes = (size_t)D * N * sizeof(float);
-    if (e == cudaSuccess) e = cudaMalloc(&s->f, population_bytes(s));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->q, qbytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&s->status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_red, ELBM_NRED * sizeof(double));
+    // stream-ordered allocations: freeing them later does not synchronise the device
+    if (e == cudaSuccess) e = cudaMallocAsync(&s->f, population_bytes(s), s->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&s->q, qbytes, s->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&s->status, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, sizeof(int), s->stream);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "elbm_create");
         elbm_destroy(s);
@@ -254,16 +254,11 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
 void elbm_destroy(elbm_solver* s)
 {
     if (!s) return;
-    if (s->stream || s->f) cudaStreamSynchronize(s->stream);
     drop_graphs(s);
-    cudaFree(s->f);
-    cudaFree(s->f2);
-    cudaFree(s->q);
-    cudaFree(s->status);
-    cudaFree(s->mom);
-    cudaFree(s->partials);
-    cudaFree(s->red_out);
-    if (s->host_red) cudaFreeHost(s->host_red);
+    // stream-ordered frees: they wait for the solver's queued work, not the device
+    for (void* ptr : {s->f, s->f2, (void*)s->q, (void*)s->status, (void*)s->mom, (void*)s->partials,
+                      (void*)s->red_out})
+        if (ptr) cudaFreeAsync(ptr, s->stream);
     delete s;
 }
 
@@ -325,13 +320,14 @@ static cudaError_t ensure_reduce_scratch(elbm_solver* s);
 
 static cudaError_t stage_to_device(const void* host, size_t bytes, void** dev, cudaStream_t st)
 {
-    cudaError_t e = cudaMalloc(dev, bytes);
+    cudaError_t e = cudaMallocAsync(dev, bytes, st);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st);
 }
 
 int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_device)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s || !rho || !u) return fail(ELBM_ERR_ARG, "NULL argument");
     if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
     const size_t es = dtype == ELBM_DTYPE_F64 ? 8 : 4;
@@ -367,10 +363,8 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
         e = (s->D == 2) ? elbm::init_impl<2>(*s, drho, du, dtype, &s->launches)
                         : elbm::init_impl<3>(*s, drho, du, dtype, &s->launches);
     if (!on_device) {
-        cudaError_t e2 = cudaStreamSynchronize(s->stream);
-        if (e == cudaSuccess) e = e2;
-        cudaFree(t1);
-        cudaFree(t2);
+        if (t1) cudaFreeAsync(t1, s->stream);
+        if (t2) cudaFreeAsync(t2, s->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "elbm_init");
     s->parity = 0;
@@ -382,6 +376,7 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
 
 int elbm_step(elbm_solver* s, int n)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
     if (n < 0) return fail(ELBM_ERR_ARG, "n must be >= 0");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_step before elbm_init");
@@ -427,6 +422,7 @@ int elbm_sync(elbm_solver* s)
 
 int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s || !rho || !u) return fail(ELBM_ERR_ARG, "NULL argument");
     if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_moments before elbm_init");
@@ -434,8 +430,8 @@ int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device)
     void *drho = rho, *du = u;
     cudaError_t e = cudaSuccess;
     if (!on_device) {
-        e = cudaMalloc(&drho, es * s->N);
-        if (e == cudaSuccess) e = cudaMalloc(&du, es * s->D * s->N);
+        e = cudaMallocAsync(&drho, es * s->N, s->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&du, es * s->D * s->N, s->stream);
     }
     if (e == cudaSuccess)
         e = (s->D == 2) ? elbm::moments_impl<2>(*s, drho, du, dtype, &s->launches)
@@ -444,38 +440,40 @@ int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device)
         if (e == cudaSuccess) e = cudaMemcpyAsync(rho, drho, es * s->N, cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, es * s->D * s->N, cudaMemcpyDeviceToHost, s->stream);
     }
+    if (!on_device) {
+        cudaFreeAsync(drho, s->stream);
+        cudaFreeAsync(du, s->stream);
+    }
     cudaError_t e2 = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = e2;
-    if (!on_device) {
-        cudaFree(drho);
-        cudaFree(du);
-    }
     if (e != cudaSuccess) return cuda_fail(e, "elbm_moments");
     return check_status(s);
 }
 
 int elbm_get_populations(elbm_solver* s, void* f, int dtype, int on_device)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s || !f) return fail(ELBM_ERR_ARG, "NULL argument");
     if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_get_populations before init");
     const size_t bytes = (dtype == ELBM_DTYPE_F64 ? 8 : 4) * (size_t)s->Q * s->N;
     void* df = f;
     cudaError_t e = cudaSuccess;
-    if (!on_device) e = cudaMalloc(&df, bytes);
+    if (!on_device) e = cudaMallocAsync(&df, bytes, s->stream);
     if (e == cudaSuccess)
         e = (s->D == 2) ? elbm::get_populations_impl<2>(*s, df, dtype, &s->launches)
                         : elbm::get_populations_impl<3>(*s, df, dtype, &s->launches);
     if (!on_device && e == cudaSuccess) e = cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (!on_device) cudaFreeAsync(df, s->stream);
     cudaError_t e2 = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = e2;
-    if (!on_device) cudaFree(df);
     if (e != cudaSuccess) return cuda_fail(e, "elbm_get_populations");
     return check_status(s);
 }
 
 int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s || !f) return fail(ELBM_ERR_ARG, "NULL argument");
     if (dtype != ELBM_DTYPE_F32 && dtype != ELBM_DTYPE_F64) return fail(ELBM_ERR_ARG, "dtype must be F32 or F64");
     const size_t bytes = (dtype == ELBM_DTYPE_F64 ? 8 : 4) * (size_t)s->Q * s->N;
@@ -489,9 +487,9 @@ int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device
     if (e == cudaSuccess)
         e = (s->D == 2) ? elbm::set_populations_impl<2>(*s, df, dtype, &s->launches)
                         : elbm::set_populations_impl<3>(*s, df, dtype, &s->launches);
+    if (tmp) cudaFreeAsync(tmp, s->stream);
     cudaError_t e2 = cudaStreamSynchronize(s->stream);
     if (e == cudaSuccess) e = e2;
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(e, "elbm_set_populations");
     s->parity = 0;
     s->initialised = 1;
@@ -503,13 +501,13 @@ static cudaError_t ensure_reduce_scratch(elbm_solver* s)
     cudaError_t e = cudaSuccess;
     if (!s->mom) {
         s->red_blocks = std::max(1, std::min(8 * s->num_sms, (int)((s->N + 255) / 256)));
-        e = cudaMalloc((void**)&s->mom, 5 * sizeof(float) * (size_t)s->N);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&s->partials, sizeof(double) * ELBM_NRED * s->red_blocks);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&s->red_out, sizeof(double) * ELBM_NRED);
+        e = cudaMallocAsync((void**)&s->mom, 5 * sizeof(float) * (size_t)s->N, s->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&s->partials, sizeof(double) * ELBM_NRED * s->red_blocks, s->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&s->red_out, sizeof(double) * ELBM_NRED, s->stream);
         if (e != cudaSuccess) {
-            cudaFree(s->mom);
-            cudaFree(s->partials);
-            cudaFree(s->red_out);
+            if (s->mom) cudaFreeAsync(s->mom, s->stream);
+            if (s->partials) cudaFreeAsync(s->partials, s->stream);
+            if (s->red_out) cudaFreeAsync(s->red_out, s->stream);
             s->mom = nullptr;
             s->partials = s->red_out = nullptr;
             return e;
@@ -521,6 +519,7 @@ static cudaError_t ensure_reduce_scratch(elbm_solver* s)
 
 int elbm_reduce(elbm_solver* s, double* out)
 {
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     if (!s || !out) return fail(ELBM_ERR_ARG, "NULL argument");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_reduce before init");
     cudaError_t e = ensure_reduce_scratch(s);

@@ -71,7 +71,7 @@ struct Solver {
     float* mom = nullptr;             // reduction scratch: rho, u[3], fmin per node
     double* partials = nullptr;       // reduction scratch: per-block FP64 partial sums
     double* red_out = nullptr;        // device copy of the ELBM_NRED results
-    double* host_red = nullptr;       // pinned host copy of the results
+    double host_red[ELBM_NRED] = {};  // host copy of the results
     int red_blocks = 0;
     long long steps_done = 0;
     long long launches = 0;
@@ -83,6 +83,13 @@ struct BatchMember {
     StepParams p;         // the member's parameter block (its parity field is ignored)
     int block_begin[2];   // first block of the member in launches of 128 and of 256 threads
     int parity;           // streaming parity before the first step of a launch sequence
+};
+
+// Device-resident description of a batch, read by the batched kernels.
+struct BatchHeader {
+    const BatchMember* members;  // `count` members sorted by first block
+    int count;
+    int blocks[2];               // total blocks for launches of 128 and of 256 threads
 };
 
 size_t storage_bytes(int storage);
@@ -102,7 +109,7 @@ template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, lon
 template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
-template <int D> cudaError_t batch_enqueue_impl(int, int, const BatchMember*, int, int, int, cudaStream_t, long long*);
+template <int D> cudaError_t batch_enqueue_impl(int, int, const BatchHeader*, int, int, cudaStream_t, long long*);
 
 }  // namespace elbm
 

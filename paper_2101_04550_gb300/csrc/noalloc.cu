@@ -79,6 +79,7 @@ extern "C" int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const doub
     if (T >= lmin2) return noalloc_fail(ELBM_ERR_UNREALIZABLE, "T >= min lam^2: rest population not positive");
     if (!(nu > 0.0) || !std::isfinite(nu)) return noalloc_fail(ELBM_ERR_ARG, "nu must be finite and > 0");
 
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return noalloc_fail(ELBM_ERR_CUDA, "no usable current device");

@@ -35,6 +35,7 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_get_populations", "elbm_set_populations", "elbm_reduce", "elbm_sync", "elbm_cells",
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
+           "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
            "elbm_step_noalloc"]
 
 
@@ -81,6 +82,9 @@ def load(build_if_missing: bool = True):
         L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
         L.elbm_batch_step.argtypes = [vp, ip]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
+        L.elbm_batch_add.argtypes = [vp, vp]
+        L.elbm_batch_remove.argtypes = [vp, vp]
+        L.elbm_batch_size.argtypes = [vp]
         L.elbm_batch_destroy.argtypes = [vp]
         L.elbm_batch_destroy.restype = None
         L.elbm_last_error.argtypes = []
@@ -265,6 +269,17 @@ class Batch:
 
     def step(self, n=1):
         _check(load().elbm_batch_step(self._h, int(n)))
+
+    def add(self, solver):
+        _check(load().elbm_batch_add(self._h, solver.handle))
+        self.solvers.append(solver)
+
+    def remove(self, solver):
+        _check(load().elbm_batch_remove(self._h, solver.handle))
+        self.solvers.remove(solver)
+
+    def __len__(self):
+        return load().elbm_batch_size(self._h)
 
     def info(self):
         bs = ctypes.c_int()

@@ -145,9 +145,9 @@ class Server:
 
         pending = collections.deque(trace)
         queue = collections.deque()
-        active = []           # [req, solver, steps_left, t_admit]
+        active = []           # [req, solver, steps_left, t_admit(, batch key once joined)]
         used = 0
-        batches = {}          # group key -> (member ids, Batch)
+        batches = {}          # (lattice, storage) -> Batch of the resident requests of that kind
         while pending or queue or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
@@ -173,33 +173,29 @@ class Server:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
             chunk = min(self.chunk_steps, min(a[2] for a in active))
-            groups = collections.defaultdict(list)
-            for a in active:
-                groups[(a[0].lattice, a[0].storage)].append(a)
-            for key, members in groups.items():
-                ids = tuple(a[0].rid for a in members)
-                if key not in batches or batches[key][0] != ids:
-                    if key in batches:
-                        batches[key][1].close()
-                    batches[key] = (ids, elbm.Batch([a[1] for a in members]))
-                batches[key][1].step(chunk)
-            for key in list(batches):
-                if key not in groups:
-                    batches.pop(key)[1].close()
+            for a in active:  # newly admitted requests join their group's batch
+                key = (a[0].lattice, a[0].storage)
+                if len(a) == 4:
+                    if key not in batches:
+                        batches[key] = elbm.Batch([a[1]])
+                    else:
+                        batches[key].add(a[1])
+                    a.append(key)
+            for b in batches.values():
+                b.step(chunk)
             still = []
             for a in active:
                 a[2] -= chunk
                 if a[2] == 0:
-                    for key, (ids, b) in list(batches.items()):
-                        if a[0].rid in ids:
-                            b.close()
-                            batches.pop(key)
+                    batches[a[4]].remove(a[1])
                     self._finish(a[0], a[1], t0, a[3])
                     used -= a[0].device_bytes()
                 else:
                     still.append(a)
             active = still
-        for _, b in batches.values():
+            for key in [k for k, b in batches.items() if len(b) == 0]:
+                batches.pop(key).close()
+        for b in batches.values():
             b.close()
         return self.summary(trace)
 

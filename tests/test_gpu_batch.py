@@ -75,3 +75,24 @@ def test_batch_rejects_mixed_storage():
         elbm.Batch([a, b])
     a.close()
     b.close()
+
+
+def test_members_join_and_leave_a_running_batch():
+    specs = SPECS3
+    solo = [_make(elbm.D3Q27, sp, elbm.F32_SHIFT, k) for k, sp in enumerate(specs)]
+    mixed = [_make(elbm.D3Q27, sp, elbm.F32_SHIFT, k) for k, sp in enumerate(specs)]
+    with elbm.Batch(mixed[:2]) as b:
+        b.step(10)
+        b.add(mixed[2])          # joins mid-flight at step 0
+        b.step(7)
+        b.remove(mixed[0])       # leaves after 17 steps
+        b.add(mixed[3])
+        b.step(7)                # replays the graph of 7 steps with new members
+        assert len(b) == 3
+    counts = [17, 24, 14, 7]
+    for s, m, k in zip(solo, mixed, counts):
+        s.step(k)
+        assert m.steps_done == k
+        assert np.array_equal(s.get_populations(), m.get_populations())
+    for s in solo + mixed:
+        s.close()

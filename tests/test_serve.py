@@ -60,10 +60,19 @@ class World:
 
         class FakeBatch:
             def __init__(self, solvers):
-                self.solvers = solvers
-                world.batch_log.append(tuple(s.req.rid for s in solvers))
+                self.solvers = list(solvers)
+
+            def add(self, s):
+                self.solvers.append(s)
+
+            def remove(self, s):
+                self.solvers.remove(s)
+
+            def __len__(self):
+                return len(self.solvers)
 
             def step(self, k):
+                world.batch_log.append(tuple(s.req.rid for s in self.solvers))
                 for s in self.solvers:
                     s.steps_done += k
                 world.clock.t += k * sum(s.N for s in self.solvers) * 1e-9 / 4  # batching fills the GPU
