@@ -186,7 +186,10 @@ long long elbm_launch_count(const elbm_solver* s);
  * Deviation, Paastar1, 27eqext) over all members; every member's result is
  * bit-identical to stepping it alone.  The batch holds the solvers (it does
  * not own them) and a device table of their parameters, refreshed at every
- * elbm_batch_step; destroy the batch before any of its solvers.
+ * elbm_batch_step; destroy the batch before any of its solvers.  A batch
+ * holds at most 40 solvers, and one live batch per (lattice, storage mode)
+ * and device may exist at a time (its member table lives in constant
+ * memory); elbm_batch_create returns ELBM_ERR_STATE for a second one.
  */
 typedef struct elbm_batch elbm_batch;
 

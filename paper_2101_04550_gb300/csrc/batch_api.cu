@@ -2,15 +2,19 @@
 // membership, the device member table, the block-size autotuner and the CUDA
 // graphs of launch sequences.
 //
-// The batched kernels read the member count, the member table and the block
-// totals from device memory, and the launch sequences are sized for the
-// batch's block capacity, so members can join and leave without a new graph:
-// only a capacity increase (or a new block size or step count) captures one.
+// The batched kernels read the member table from constant memory (one table
+// per storage mode, refreshed before each launch sequence), so a live batch
+// owns the table of its (lattice, storage) kind: one live batch per kind and
+// device.  A launch sequence of n steps is captured once as a CUDA graph; when
+// membership changes the block total, the graph is re-captured and the
+// executable graph updated in place.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -19,18 +23,18 @@
 struct elbm_batch {
     std::vector<elbm_solver*> members;
     std::vector<elbm::BatchMember> table;
-    elbm::BatchHeader header{};
-    unsigned char* d_buf = nullptr;    // header, then the member table
-    size_t d_capacity = 0;             // members the device buffer holds
-    int lattice = 0, storage = 0, D = 0;
+    int lattice = 0, storage = 0, D = 0, device = 0;
     int blocks[2] = {0, 0};            // current block totals (128, 256 threads)
-    int grid[2] = {0, 0};              // block capacity the graphs were captured for
     cudaStream_t stream = nullptr;      // the members' stream
     cudaStream_t exec_stream = nullptr; // private stream that captures and replays graphs
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int block_size = 0;                // chosen by the autotuner
     float tuned_ms[2] = {0, 0};
-    std::map<int, cudaGraphExec_t> graphs;  // by step count, for block_size and grid
+    struct Seq {
+        cudaGraphExec_t exec = nullptr;
+        int grid = 0;                  // block total it was captured for
+    };
+    std::map<int, Seq> graphs;         // launch sequences by step count
     long long launches = 0;
 };
 
@@ -49,10 +53,13 @@ int bcuda(cudaError_t e, const char* what)
 // batch of the process: the first batch of a kind pays the two tuning steps.
 std::mutex g_tune_lock;
 std::map<std::pair<int, int>, int> g_tuned;
+// Kinds (device, lattice, storage) with a live batch: each owns a constant table.
+std::set<std::tuple<int, int, int>> g_live;
 
 void drop_graphs(elbm_batch* b)
 {
-    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : b->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     b->graphs.clear();
 }
 
@@ -68,8 +75,9 @@ cudaError_t join_out(elbm_batch* b)
 }
 
 // Recompute the block layout, refresh every member's parameter block and
-// parity, and upload header and table (on the private stream, ordered before
-// the next launch sequence).
+// parity, and upload the table to the constant memory of the batch's kind (on
+// the private stream, ordered before the next launch sequence; copies from
+// pageable memory return once the source has been read).
 cudaError_t upload(elbm_batch* b)
 {
     const size_t n = b->members.size();
@@ -86,35 +94,14 @@ cudaError_t upload(elbm_batch* b)
     }
     b->blocks[0] = (int)begin128;
     b->blocks[1] = (int)begin256;
-    if (n > b->d_capacity) {
-        const size_t cap = std::max<size_t>(2 * b->d_capacity, std::max<size_t>(n, 8));
-        unsigned char* nb = nullptr;
-        cudaError_t e = cudaMallocAsync((void**)&nb, sizeof(elbm::BatchHeader) + cap * sizeof(elbm::BatchMember),
-                                        b->exec_stream);
-        if (e != cudaSuccess) return e;
-        if (b->d_buf) cudaFreeAsync(b->d_buf, b->exec_stream);
-        b->d_buf = nb;
-        b->d_capacity = cap;
-        drop_graphs(b);  // the graphs point at the old buffer
-    }
-    b->header.members = reinterpret_cast<const elbm::BatchMember*>(b->d_buf + sizeof(elbm::BatchHeader));
-    b->header.count = (int)n;
-    b->header.blocks[0] = b->blocks[0];
-    b->header.blocks[1] = b->blocks[1];
-    cudaError_t e = cudaMemcpyAsync(b->d_buf, &b->header, sizeof(b->header), cudaMemcpyHostToDevice, b->exec_stream);
-    if (e == cudaSuccess && n)
-        e = cudaMemcpyAsync(b->d_buf + sizeof(elbm::BatchHeader), b->table.data(), n * sizeof(elbm::BatchMember),
-                            cudaMemcpyHostToDevice, b->exec_stream);
-    // (copies from pageable memory return once the source has been read, so
-    // the host table may be rewritten by the next upload)
-    return e;
+    return (b->D == 2) ? elbm::batch_upload_impl<2>(b->storage, b->table.data(), (int)n, b->exec_stream)
+                       : elbm::batch_upload_impl<3>(b->storage, b->table.data(), (int)n, b->exec_stream);
 }
 
 cudaError_t enqueue(elbm_batch* b, int block_size, int grid, int nsteps)
 {
-    const auto* h = reinterpret_cast<const elbm::BatchHeader*>(b->d_buf);
-    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, h, grid, nsteps, b->exec_stream, &b->launches)
-                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, h, grid, nsteps, b->exec_stream, &b->launches);
+    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, grid, nsteps, b->exec_stream, &b->launches)
+                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, grid, nsteps, b->exec_stream, &b->launches);
 }
 
 void advance_members(elbm_batch* b, int nsteps)
@@ -172,6 +159,7 @@ int check_member(const elbm_batch* b, const elbm_solver* s)
     if (s->stream != b->stream) return bfail(ELBM_ERR_ARG, "batch members must share one stream");
     if (std::find(b->members.begin(), b->members.end(), s) != b->members.end())
         return bfail(ELBM_ERR_ARG, "solver listed twice in batch");
+    if ((int)b->members.size() >= elbm::kBatchMax) return bfail(ELBM_ERR_ARG, "a batch holds at most 40 solvers");
     return ELBM_OK;
 }
 
@@ -192,6 +180,7 @@ int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out)
     b->storage = solvers[0]->storage;
     b->D = solvers[0]->D;
     b->stream = solvers[0]->stream;
+    b->device = solvers[0]->device;
     for (int k = 0; k < n; ++k) {
         const int rc = check_member(b, solvers[k]);
         if (rc != ELBM_OK) {
@@ -202,6 +191,10 @@ int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out)
     }
     {
         std::lock_guard<std::mutex> lock(g_tune_lock);
+        if (!g_live.insert({b->device, b->lattice, b->storage}).second) {
+            delete b;
+            return bfail(ELBM_ERR_STATE, "a batch of this lattice and storage mode is already live on this device");
+        }
         auto it = g_tuned.find({b->lattice, b->storage});
         if (it != g_tuned.end()) b->block_size = it->second;
     }
@@ -249,30 +242,35 @@ int elbm_batch_step(elbm_batch* b, int nsteps)
     }
     if (left == 0) return ELBM_OK;
     const int bs = b->block_size ? b->block_size : 256, idx = bs == 128 ? 0 : 1;
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
     cudaError_t e = join_in(b);
     if (e == cudaSuccess) e = upload(b);
-    if (e == cudaSuccess && b->blocks[idx] > b->grid[idx]) {
-        // capacity: twice the current need, so that joining members rarely recapture
-        b->grid[idx] = std::max(2 * b->blocks[idx], 1);
-        drop_graphs(b);
-    }
     cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) {
-        auto it = b->graphs.find(left);
-        if (it != b->graphs.end()) {
-            exec = it->second;
-        } else {
+        elbm_batch::Seq& seq = b->graphs[left];
+        if (!seq.exec || seq.grid != b->blocks[idx]) {
+            // capture the launch sequence for the current block total; update
+            // the executable graph in place when it exists
             cudaGraph_t g = nullptr;
             e = cudaStreamBeginCapture(b->exec_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t e1 = enqueue(b, bs, b->grid[idx], left);
+                const cudaError_t e1 = enqueue(b, bs, b->blocks[idx], left);
                 e = cudaStreamEndCapture(b->exec_stream, &g);
                 if (e == cudaSuccess) e = e1;
             }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+            if (e == cudaSuccess && seq.exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(seq.exec, g, &info) != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    cudaGraphExecDestroy(seq.exec);
+                    seq.exec = nullptr;
+                }
+            }
+            if (e == cudaSuccess && !seq.exec) e = cudaGraphInstantiate(&seq.exec, g, 0);
             if (g) cudaGraphDestroy(g);
-            if (e == cudaSuccess) b->graphs[left] = exec;
+            if (e == cudaSuccess) seq.grid = b->blocks[idx];
         }
+        exec = seq.exec;
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(exec, b->exec_stream);
     if (e == cudaSuccess) e = join_out(b);
@@ -301,7 +299,10 @@ void elbm_batch_destroy(elbm_batch* b)
     if (!b) return;
     if (b->exec_stream) cudaStreamSynchronize(b->exec_stream);
     drop_graphs(b);
-    if (b->d_buf) cudaFree(b->d_buf);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        g_live.erase({b->device, b->lattice, b->storage});
+    }
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->exec_stream) cudaStreamDestroy(b->exec_stream);

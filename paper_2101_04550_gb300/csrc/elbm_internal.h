@@ -85,12 +85,8 @@ struct BatchMember {
     int parity;           // streaming parity before the first step of a launch sequence
 };
 
-// Device-resident description of a batch, read by the batched kernels.
-struct BatchHeader {
-    const BatchMember* members;  // `count` members sorted by first block
-    int count;
-    int blocks[2];               // total blocks for launches of 128 and of 256 threads
-};
+// Members of one batch at most (the constant-memory table of a storage mode).
+constexpr int kBatchMax = 40;
 
 size_t storage_bytes(int storage);
 // Record the message elbm_last_error() returns on the calling thread; returns code.
@@ -109,7 +105,8 @@ template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, lon
 template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
-template <int D> cudaError_t batch_enqueue_impl(int, int, const BatchHeader*, int, int, cudaStream_t, long long*);
+template <int D> cudaError_t batch_enqueue_impl(int, int, int, int, cudaStream_t, long long*);
+template <int D> cudaError_t batch_upload_impl(int, const BatchMember*, int, cudaStream_t);
 
 }  // namespace elbm
 

@@ -24,6 +24,7 @@ import numpy as np
 from . import elbm, inputs
 
 Q_BYTES = {elbm.F32: 4, elbm.F32_SHIFT: 4, elbm.F16_SHIFT: 2, elbm.BF16_SHIFT: 2}
+BATCH_MAX = 40  # members of one batch at most
 
 
 @dataclasses.dataclass
@@ -152,7 +153,9 @@ class Server:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
-            while queue and len(active) < self.max_active and used + queue[0].device_bytes() <= self.hbm_budget:
+            kinds = collections.Counter((a[0].lattice, a[0].storage) for a in active)
+            while (queue and len(active) < self.max_active and used + queue[0].device_bytes() <= self.hbm_budget
+                   and kinds[(queue[0].lattice, queue[0].storage)] < BATCH_MAX):
                 req = queue[0]
                 try:
                     solver = self._start(req)
@@ -163,6 +166,7 @@ class Server:
                     break  # out of memory while others run: retry once some finish
                 queue.popleft()
                 used += req.device_bytes()
+                kinds[(req.lattice, req.storage)] += 1
                 active.append([req, solver, req.steps, self.clock() - t0])
             if not active:
                 if queue and used + queue[0].device_bytes() > self.hbm_budget:
