@@ -68,7 +68,8 @@ extern "C" {
 /* ----------------------------------------------------------- options */
 /* ELBM_OPT_EQUILIBRIUM: 0 = extended equilibrium (Eq. 27eqext, default);
  *   1 = product-form equilibrium without the correction (Eq. 27eq);
- *   2 = product form truncated to second order in u (Sec. III preamble). */
+ *   2 = product form truncated to second order in u (the conventional
+ *       equilibrium of Sec. III preamble; two-pass form, rest storage baseline). */
 #define ELBM_OPT_EQUILIBRIUM 1
 /* ELBM_OPT_KERNEL: the form of the step; every form evaluates the same per-node
  *   arithmetic and gives bit-identical results.

@@ -157,8 +157,9 @@ void drop_graphs(elbm_solver* s)
     }
 }
 
-// Kernel form a step uses: 0 (automatic) means the two-pass form.
-int effective_kernel(const elbm_solver* s) { return s->kernel != 0 ? s->kernel : 1; }
+// Kernel form a step uses: 0 (automatic) means the two-pass form, which is
+// also the only form of the second-order equilibrium.
+int effective_kernel(const elbm_solver* s) { return (s->kernel != 0 && s->eq_mode != 2) ? s->kernel : 1; }
 
 size_t population_bytes(const elbm_solver* s)
 {
@@ -268,7 +269,9 @@ int elbm_set_option(elbm_solver* s, int key, double value)
     drop_graphs(s);
     switch (key) {
         case ELBM_OPT_EQUILIBRIUM:
-            if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "equilibrium must be 0 or 1");
+            if (value != 0.0 && value != 1.0 && value != 2.0) return fail(ELBM_ERR_ARG, "equilibrium must be 0, 1 or 2");
+            if (value == 2.0 && (s->u_ref_auto || s->u_ref[0] != 0.0 || s->u_ref[1] != 0.0 || s->u_ref[2] != 0.0))
+                return fail(ELBM_ERR_ARG, "the second-order equilibrium needs the rest storage baseline (U0 = 0)");
             s->eq_mode = (int)value;
             return ELBM_OK;
         case ELBM_OPT_KERNEL: {
@@ -292,6 +295,8 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             if (!std::isfinite(value)) return fail(ELBM_ERR_ARG, "baseline velocity must be finite");
             if (s->initialised) return fail(ELBM_ERR_STATE, "the baseline velocity must be set before init");
             if (a >= s->D) return value == 0.0 ? ELBM_OK : fail(ELBM_ERR_ARG, "no such axis for this lattice");
+            if (s->eq_mode == 2 && value != 0.0)
+                return fail(ELBM_ERR_ARG, "the second-order equilibrium needs the rest storage baseline (U0 = 0)");
             float tri[3];
             double ueff;
             if (!elbm::base_triplet(s->T, s->lam[a], value, tri, &ueff))

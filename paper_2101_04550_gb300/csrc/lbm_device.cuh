@@ -292,6 +292,54 @@ __device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float 
     }
 }
 
+// The conventional second-order equilibrium (Sec. III preamble): the product
+// form of Eq. 27eq with every term of total degree above two in u dropped.
+// Per axis Psi_c(u, T + u^2, lam) = A_c + B_c u + C_c u^2 with A_c the rest
+// triplet, B_{+-1} = +-1/(2 lam), B_0 = 0, C_{+-1} = 1/(2 lam^2), C_0 = -1/lam^2,
+// so with l_a = B u_a and s_a = (B + C u_a) u_a the truncated product is
+//   S_i = w_i + sum_a s_a prod_{b != a} A_b + sum_{a<b} l_a l_b prod_{c != a,b} A_c,
+// and fn(i, rho S_i - rho_ref w_i) = fn(i, drho w_i + rho (S_i - w_i)).
+// Defined for the rest baseline (U0 = 0), where base = rest triplet.
+template <int D, typename F>
+__device__ __forceinline__ void for_each_second_order(const StepParams& p, float drho, const float* u, F&& fn)
+{
+    const float rho = p.rho_ref + drho;
+    float A[3][3], l[3][3], sq[3][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float hb = 0.5f * p.inv_lam[a] * u[a];
+        const float q2 = u[a] * u[a] * p.inv_lam2[a];
+        l[a][0] = -hb;
+        l[a][1] = 0.f;
+        l[a][2] = hb;
+        sq[a][0] = fmaf(0.5f, q2, -hb);
+        sq[a][1] = -q2;
+        sq[a][2] = fmaf(0.5f, q2, hb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A[a][c] = p.base[a][c];
+    }
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy) {
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+            if (D == 2) {
+                const float dev = sq[0][cx] * A[1][cy] + sq[1][cy] * A[0][cx] + l[0][cx] * l[1][cy];
+                const int i = cx + 3 * cy;
+                fn(i, fmaf(drho, p.bw[i], rho * dev));
+            } else {
+#pragma unroll
+                for (int cz = 0; cz < 3; ++cz) {
+                    const float dev = sq[0][cx] * A[1][cy] * A[2][cz] + sq[1][cy] * A[0][cx] * A[2][cz] +
+                                      sq[2][cz] * A[0][cx] * A[1][cy] + l[0][cx] * l[1][cy] * A[2][cz] +
+                                      l[0][cx] * l[2][cz] * A[1][cy] + l[1][cy] * l[2][cz] * A[0][cx];
+                    const int i = cx + 3 * cy + 9 * cz;
+                    fn(i, fmaf(drho, p.bw[i], rho * dev));
+                }
+            }
+        }
+    }
+}
+
 // Per-axis arguments of for_each_equilibrium for velocity u and pressure
 // excess over T, pex = P - T: du = u - U0, dP = pex - U0^2 = du (u + U0) + (pex - u^2).
 template <int D>

@@ -67,7 +67,8 @@ __device__ __forceinline__ void moments_of(const StepParams& p, G&& gval, float&
 // Relaxation of one node toward the extended equilibrium with the
 // conservation correction of relax(), for populations read through gval(i)
 // (read twice, not kept in registers) and results handed to put(i, g'_i).
-template <int D, typename G, typename P>
+// POLY selects the conventional second-order equilibrium instead.
+template <int D, bool POLY = false, typename G, typename P>
 __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&& put, float drho,
                                                const float* j, const float* d)
 {
@@ -84,7 +85,7 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     const float om = p.omega;
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
     float keep[2 * D + 1];
-    for_each_equilibrium<D>(p, drho, du, dP, [&](int i, float geq) {
+    auto relax_one = [&](int i, float geq) {
         const float gi = gval(i);
         const float dl = geq - gi;
         e0 += dl;
@@ -97,7 +98,9 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
         const int k = corrected_slot<D>(i);
         if (k >= 0) keep[k] = geq;
         else put(i, fmaf(om, dl, gi));
-    });
+    };
+    if (POLY) for_each_second_order<D>(p, drho, u, relax_one);
+    else for_each_equilibrium<D>(p, drho, du, dP, relax_one);
     const float hx = 0.5f * ex, hy = 0.5f * ey;
     put(I0, fmaf(om, (keep[0] - gval(I0)) - e0, gval(I0)));
     put(I0 - 1, fmaf(om, (keep[1] - gval(I0 - 1)) + hx, gval(I0 - 1)));
@@ -118,7 +121,7 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
 // Populations are read back from the stage instead of being held in
 // registers, which keeps the register count low enough for 32 resident
 // warps per SM.
-template <int D, int ST, int PAR, int STRIDE = kBlock>
+template <int D, int ST, int PAR, int STRIDE = kBlock, bool POLY = false>
 __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, unsigned* col)
 {
     constexpr int Q = Lat<D>::Q;
@@ -148,17 +151,18 @@ __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, un
         const int slot = (PAR == 0) ? (Q - 1 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
         S::store(f + slot, S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn));
     };
-    relax_streamed<D>(p, gval, put, drho, j, d);
+    relax_streamed<D, POLY>(p, gval, put, drho, j, d);
 }
 
-// Pass 2 over every node: one node per thread, populations staged in shared memory.
-template <int D, int ST, int PAR>
+// Pass 2 over every node: one node per thread, populations staged in shared
+// memory.  POLY: the conventional second-order equilibrium (no anomaly pass).
+template <int D, int ST, int PAR, bool POLY = false>
 __global__ void __launch_bounds__(kBlock, ELBM_COLLIDE_MIN_BLOCKS) k_collide(StepParams p)
 {
     __shared__ unsigned stage[Lat<D>::Q * kBlock];
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
-    collide_staged<D, ST, PAR>(p, cell, stage + threadIdx.x);
+    collide_staged<D, ST, PAR, kBlock, POLY>(p, cell, stage + threadIdx.x);
 }
 
 template <int D>
@@ -170,7 +174,10 @@ cudaError_t step_two_pass_impl(const Solver& s, int parity, long long* launches)
     const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
     const dim3 cgrid = grid;
     ELBM_DISPATCH_STORAGE(s.storage, {
-        if (parity == 0) {
+        if (p.eq_mode == 2) {
+            if (parity == 0) k_collide<D, ST, 0, true><<<cgrid, kBlock, 0, s.stream>>>(p);
+            else k_collide<D, ST, 1, true><<<cgrid, kBlock, 0, s.stream>>>(p);
+        } else if (parity == 0) {
             if (p.eq_mode == 0) { k_anomaly<D, ST, 0><<<grid, kBlock, 0, s.stream>>>(p); ++*launches; }
             k_collide<D, ST, 0><<<cgrid, kBlock, 0, s.stream>>>(p);
         } else {

@@ -95,6 +95,19 @@ def test_d2q9_product_form_mode():
     assert rel_linf(ug, uo) <= 1e-5
 
 
+@pytest.mark.parametrize("lattice,n,lam", [(elbm.D2Q9, (64, 64), (1.0, 1.0)),
+                                           (elbm.D3Q27, (24, 16, 20), (1.0, 1.5, 2.0))])
+def test_second_order_equilibrium_mode(lattice, n, lam):
+    """The conventional second-order equilibrium (Sec. III preamble) against
+    the oracle's, on an advected rotated wave."""
+    D = 2 if lattice == elbm.D2Q9 else 3
+    kd, sd = ((1, 1), (-1, 1)) if D == 2 else ((1, 0, 1), (-1, 0, 1))
+    rho, u, _, _ = inputs.shear_wave(n, lam, kd, sd, 1e-2, 0.1)
+    _, ug = run_gpu(lattice, n, lam, 0.4, 0.02, rho, u, 300, elbm.F32_SHIFT, 1, equilibrium=2)
+    _, uo = run_oracle(D, n, lam, 0.4, 0.02, rho, u, 300, mode=oracle.SECOND_ORDER)
+    assert rel_linf(ug, uo) <= 1e-5
+
+
 @pytest.mark.parametrize("storage", [elbm.F16_SHIFT, elbm.BF16_SHIFT])
 def test_d2q9_half_storage_advected(storage):
     """Half-precision storage of an advected rotated wave (U = 0.1, amplitude
