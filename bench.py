@@ -33,6 +33,13 @@ import numpy as np  # noqa: E402
 WORKLOAD = dict(workload="D3Q27 decaying isotropic turbulence 256^3 periodic", lattice="D3Q27",
                 nx=256, ny=256, nz=256, stretch=[1.0, 1.0, 1.0], T=1.0 / 3.0, nu=0.0233,
                 u_rms=0.08, k0=4.0, seed=0)
+# Wall-bounded turbulent channel (Sec. III.E): Re_tau = 180, H = 64 nodes of
+# lam_y = 1, u_tau = 0.1 / (ln(180)/0.41 + 5.5), nu = u_tau H / 180,
+# g = u_tau^2 / H, laminar profile of centre-line velocity 0.1 plus a seeded 5 %
+# perturbation.
+CHANNEL = dict(workload="D3Q27 turbulent channel 512x128x256, lam=(2,1,2), walls in y, body force",
+               nx=512, ny=128, nz=256, stretch=[2.0, 1.0, 2.0], T=0.55, u_tau=0.1 / (np.log(180.0) / 0.41 + 5.5))
+CHANNEL.update(nu=CHANNEL["u_tau"] * 64 / 180.0, g=CHANNEL["u_tau"] ** 2 / 64)
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {0: "two-pass", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
 KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range",
@@ -372,6 +379,36 @@ def main():
             variants[name] = {"MLUPS": cells * nsteps / tot / 1e6,
                               "step_MLUPS": cells * nsteps / sts / 1e6,
                               "roofline_frac": cells * nsteps * b / sts / 1e9 / peak}
+
+    # ---- the channel configuration: walls + body force (two-pass) -------
+    if not args.no_variants and rank == 0 and args.nodes == 256:
+        from paper_2101_04550_gb300 import inputs
+        c = CHANNEL
+        nch = (c["nx"], c["ny"], c["nz"])
+        crho, cu = inputs.channel(nch, tuple(c["stretch"]), u_center=0.1, perturbation=0.05, seed=0)
+        stream = torch.cuda.current_stream()
+        for name, st in (("channel_f32_shift", elbm.F32_SHIFT), ("channel_f32", elbm.F32)):
+            sc = elbm.Solver(elbm.D3Q27, nch, stretch=c["stretch"], T=c["T"], nu=c["nu"], storage=st,
+                             stream=stream, walls_y=True, force=(c["g"], 0.0, 0.0))
+            sc.init(torch.as_tensor(crho, device="cuda"), torch.as_tensor(cu, device="cuda"))
+            sc.step(args.warmup)
+            sc.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            nsteps = min(args.steps, 200)
+            a.record(stream)
+            sc.step(nsteps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            red = sc.reduce()
+            sc.close()
+            sts = a.elapsed_time(b) / 1e3
+            ncell = nch[0] * nch[1] * nch[2]
+            bb = 2 * Q * elbm.STORAGE_BYTES[st]
+            variants[name] = {"MLUPS": ncell * nsteps / sts / 1e6, "step_MLUPS": ncell * nsteps / sts / 1e6,
+                              "roofline_frac": ncell * nsteps * bb / sts / 1e9 / peak,
+                              "workload": c["workload"], "finite": red["nonfinite"] == 0}
+        del crho, cu
 
     # ---- CPU baseline (oracle), rank 0 at N = 1 only ---------------------
     cpu = None

@@ -109,8 +109,14 @@ extern "C" {
  *  [0] sum rho          [1..3] sum rho u_a        [4] sum rho |u|^2
  *  [5] sum |u|^2        [6] sum |curl u|^2 (central differences, spacing lam)
  *  [7] sum (d_x u_x)^2  [8] sum u_x^2             [9] min_i,x f_i (realizability)
- *  [10] number of nodes with a non-finite rho or u  [11] max |u|                   */
-#define ELBM_NRED 12
+ *  [10] number of nodes with a non-finite rho or u  [11] max |u|
+ *  [12] with walls: sum over the nodes next to either wall of the wall-normal
+ *       gradient of u_x, (9 u_x(first node) - u_x(second node)) / (3 lam_y)
+ *       (quadratic through the no-slip wall half a spacing away); the mean
+ *       wall shear stress is rho nu [12] / (2 nx nz).  0 without walls.
+ *  With walls, y-differences take the velocity beyond a wall as the negated
+ *  value of the wall-adjacent node.                                            */
+#define ELBM_NRED 13
 
 typedef struct elbm_solver elbm_solver;
 

@@ -157,6 +157,9 @@ int check_member(const elbm_batch* b, const elbm_solver* s)
     if (s->lattice != b->lattice || s->storage != b->storage)
         return bfail(ELBM_ERR_ARG, "batch members must share lattice and storage mode");
     if (s->stream != b->stream) return bfail(ELBM_ERR_ARG, "batch members must share one stream");
+    if (s->eq_mode == 2 || s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0)
+        return bfail(ELBM_ERR_ARG, "the batched step takes periodic, unforced solvers with the extended or "
+                                   "product-form equilibrium");
     if (std::find(b->members.begin(), b->members.end(), s) != b->members.end())
         return bfail(ELBM_ERR_ARG, "solver listed twice in batch");
     if ((int)b->members.size() >= elbm::kBatchMax) return bfail(ELBM_ERR_ARG, "a batch holds at most 40 solvers");

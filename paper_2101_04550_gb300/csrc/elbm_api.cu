@@ -121,6 +121,7 @@ void fill_params(const Solver& s, StepParams& p)
     p.rho_ref = (float)s.rho_ref;
     for (int a = 0; a < 3; ++a) p.g[a] = (float)s.g[a];
     p.forced = (s.g[0] != 0.0 || s.g[1] != 0.0 || s.g[2] != 0.0);
+    p.walls_y = s.walls_y;
     p.eq_mode = s.eq_mode;
     p.parity = s.parity;
 }
@@ -159,7 +160,12 @@ void drop_graphs(elbm_solver* s)
 
 // Kernel form a step uses: 0 (automatic) means the two-pass form, which is
 // also the only form of the second-order equilibrium.
-int effective_kernel(const elbm_solver* s) { return (s->kernel != 0 && s->eq_mode != 2) ? s->kernel : 1; }
+// The second-order equilibrium, walls and the body force run in the two-pass form.
+int effective_kernel(const elbm_solver* s)
+{
+    const bool special = s->eq_mode == 2 || s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
+    return (s->kernel != 0 && !special) ? s->kernel : 1;
+}
 
 size_t population_bytes(const elbm_solver* s)
 {
@@ -312,10 +318,17 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             return ELBM_OK;
         case ELBM_OPT_FORCE_X:
         case ELBM_OPT_FORCE_Y:
-        case ELBM_OPT_FORCE_Z:
+        case ELBM_OPT_FORCE_Z: {
+            const int a = key - ELBM_OPT_FORCE_X;
+            if (!std::isfinite(value)) return fail(ELBM_ERR_ARG, "body force must be finite");
+            if (a >= s->D) return value == 0.0 ? ELBM_OK : fail(ELBM_ERR_ARG, "no such axis for this lattice");
+            s->g[a] = value;
+            return ELBM_OK;
+        }
         case ELBM_OPT_WALLS_Y:
-            if (value == 0.0) return ELBM_OK;
-            return fail(ELBM_ERR_ARG, "option %d is not supported by this build", key);
+            if (value != 0.0 && value != 1.0) return fail(ELBM_ERR_ARG, "walls_y must be 0 or 1");
+            s->walls_y = (int)value;
+            return ELBM_OK;
         default:
             return fail(ELBM_ERR_ARG, "unknown option %d", key);
     }

@@ -40,6 +40,7 @@ struct StepParams {
     float rho_ref;        // reference density of the shifted storage
     float g[3];           // body-force acceleration
     int forced;           // g != 0
+    int walls_y;          // half-way bounce-back walls below y = 0 and above y = ny-1
     int eq_mode;          // 0 extended, 1 product form, 2 second order
     int parity;           // AA streaming parity of the step about to run (0 even, 1 odd)
 };
@@ -97,6 +98,7 @@ void fill_params(const Solver& s, StepParams& p);
 // kernels_d3q27.cu).  Each returns the CUDA error of its launches and adds the
 // number of kernel launches it issued to *launches.
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
+template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);

@@ -69,6 +69,7 @@ struct Storage<ELBM_BF16_SHIFT> {
 struct Node {
     int cell;
     int ox[3], oy[3], oz[3];
+    bool ylo, yhi;  // first / last node along y (next to a wall when walls are on)
     __device__ int at(int cx, int cy, int cz) const { return ox[cx + 1] + oy[cy + 1] + oz[cz + 1]; }
 };
 
@@ -94,6 +95,8 @@ __device__ __forceinline__ Node make_node(const StepParams& p, int cell)
     n.oy[1] = y * p.nx;
     n.oy[0] = ((y == 0) ? p.ny - 1 : y - 1) * p.nx;
     n.oy[2] = ((y == p.ny - 1) ? 0 : y + 1) * p.nx;
+    n.ylo = (y == 0);
+    n.yhi = (y == p.ny - 1);
     if (D == 3) {
         n.oz[1] = z * p.plane;
         n.oz[0] = ((z == 0) ? p.nz - 1 : z - 1) * p.plane;
@@ -111,42 +114,75 @@ __device__ __forceinline__ Node make_node(const StepParams& p, int cell)
 // (opp(i), x - c_i) and the step writes to slot (i, x + c_i).  Either way a node
 // reads and writes the same slot set, and the slot sets of distinct nodes are
 // disjoint (Eq. LBGK: f_i moves one node along c_i per step).
+//
+// With walls below y = 0 and above y = ny-1 (half-way bounce-back) a
+// population that would cross a wall comes back reversed to the node it left:
+// f_i(x, t+1) = f'_opp(i)(x, t).  The even step needs no change (it touches
+// only the node's own slots).  In the odd step, f_i(x) with x - c_i beyond a
+// wall is f'_opp(i)(x), which the even step left in slot (i, x); and f'_i(x)
+// with x + c_i beyond a wall becomes f_opp(i)(x) of the next step, slot
+// (opp(i), x).  Reads and writes of a node still cover one and the same slot
+// set: population i is bounced on reading exactly when opp(i) is bounced on
+// writing.
+//
+// A stored deviation is taken against the baseline of the population it
+// holds, so a bounced population, which changes from opp(i) to i, is rebased
+// by rho_ref (b_opp(i) - b_i) on reading and by rho_ref (b_i - b_opp(i)) on
+// writing (zero for the rest baseline, which is symmetric).
+__device__ __forceinline__ bool read_bounced(const Node& n, int i)
+{
+    return (cy_of(i) == 1 && n.ylo) || (cy_of(i) == -1 && n.yhi);
+}
+__device__ __forceinline__ bool write_bounced(const Node& n, int i)
+{
+    return (cy_of(i) == 1 && n.yhi) || (cy_of(i) == -1 && n.ylo);
+}
 template <int D>
-__device__ __forceinline__ int read_slot(const Node& n, int N, int i, int parity)
+__device__ __forceinline__ int read_slot(const Node& n, int N, int i, int parity, bool walls = false)
 {
     constexpr int Q = Lat<D>::Q;
     if (parity == 0) return i * N + n.cell;
+    if (walls && read_bounced(n, i)) return i * N + n.cell;
     return (Q - 1 - i) * N + n.at(-cx_of(i), -cy_of(i), -cz_of<D>(i));
 }
 template <int D>
-__device__ __forceinline__ int write_slot(const Node& n, int N, int i, int parity)
+__device__ __forceinline__ int write_slot(const Node& n, int N, int i, int parity, bool walls = false)
 {
     constexpr int Q = Lat<D>::Q;
     if (parity == 0) return (Q - 1 - i) * N + n.cell;
+    if (walls && write_bounced(n, i)) return (Q - 1 - i) * N + n.cell;
     return i * N + n.at(cx_of(i), cy_of(i), cz_of<D>(i));
+}
+// Rebase of a bounced read of population i: rho_ref (b_opp(i) - b_i).
+template <int D>
+__device__ __forceinline__ float bounce_rebase(const StepParams& p, int i)
+{
+    return p.rho_ref * (p.bw[Lat<D>::Q - 1 - i] - p.bw[i]);
 }
 
 template <int D, int ST, int PAR>
-__device__ __forceinline__ void gather(const StepParams& p, const Node& n, float* g)
+__device__ __forceinline__ void gather(const StepParams& p, const Node& n, float* g, bool walls = false)
 {
     using S = Storage<ST>;
     const typename S::T* f = static_cast<const typename S::T*>(p.f);
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
-        const float v = S::load(f + read_slot<D>(n, p.N, i, PAR));
+        const float v = S::load(f + read_slot<D>(n, p.N, i, PAR, walls));
         g[i] = S::shifted ? v : v - p.bw[i] * p.rho_ref;
+        if (S::shifted && PAR == 1 && walls && read_bounced(n, i)) g[i] += bounce_rebase<D>(p, i);
     }
 }
 
 template <int D, int ST, int PAR>
-__device__ __forceinline__ void scatter(const StepParams& p, const Node& n, const float* g)
+__device__ __forceinline__ void scatter(const StepParams& p, const Node& n, const float* g, bool walls = false)
 {
     using S = Storage<ST>;
     typename S::T* f = static_cast<typename S::T*>(p.f);
 #pragma unroll
     for (int i = 0; i < Lat<D>::Q; ++i) {
-        const float v = S::shifted ? g[i] : g[i] + p.bw[i] * p.rho_ref;
-        S::store(f + write_slot<D>(n, p.N, i, PAR), v);
+        float v = S::shifted ? g[i] : g[i] + p.bw[i] * p.rho_ref;
+        if (S::shifted && PAR == 1 && walls && write_bounced(n, i)) v += bounce_rebase<D>(p, Lat<D>::Q - 1 - i);
+        S::store(f + write_slot<D>(n, p.N, i, PAR, walls), v);
     }
 }
 
@@ -352,6 +388,49 @@ __device__ __forceinline__ void baseline_args(const StepParams& p, const float* 
         dP[a] = fmaf(du[a], u[a] + p.u0[a], corr[a]);
     }
 }
+
+// Body-force increment of the exact-difference reading of the forcing,
+// F_i = rho [Psi_i(u + g, T + (u + g)^2, lam) - Psi_i(u, T + u^2, lam)] (the
+// product-form equilibrium of Eqs. prod, 27eq at the shifted and the unshifted
+// velocity), handed out divided by omega so that it joins the increment
+// omega (f*_i - f_i) before the one rounding of the relaxation.  The
+// difference of the products is telescoped over the axes,
+//   prod_a A_a - prod_a B_a = sum_a (prod_{b<a} A_b) (A_a - B_a) (prod_{b>a} B_b),
+// with A the triplet at u + g, B at u, and per axis, for dP = g (2u + g),
+//   A_0 - B_0 = -dP / lam^2,  A_{+-1} - B_{+-1} = (+-g / lam + dP / lam^2) / 2,
+// so the small increment carries no cancellation.
+template <int D>
+struct ForceIncrement {
+    float A[3][3], B[3][3], dl[3][3];
+
+    __device__ __forceinline__ void init(const StepParams& p, float rho_over_omega, const float* u)
+    {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float ua = u[a], ga = p.g[a], ug = ua + ga;
+            const float il = p.inv_lam[a], il2 = p.inv_lam2[a];
+            const float sb = fmaf(ua, ua, p.T) * il2, sa = fmaf(ug, ug, p.T) * il2;
+            B[a][0] = 0.5f * (sb - ua * il);
+            B[a][1] = 1.0f - sb;
+            B[a][2] = 0.5f * (sb + ua * il);
+            A[a][0] = 0.5f * (sa - ug * il);
+            A[a][1] = 1.0f - sa;
+            A[a][2] = 0.5f * (sa + ug * il);
+            const float s = ga * (ua + ug) * il2, t = ga * il;
+            dl[a][0] = rho_over_omega * (0.5f * (s - t));
+            dl[a][1] = rho_over_omega * (-s);
+            dl[a][2] = rho_over_omega * (0.5f * (s + t));
+        }
+    }
+    // F_i / omega for population i
+    __device__ __forceinline__ float operator()(int i) const
+    {
+        const int x = cx_of(i) + 1, y = cy_of(i) + 1;
+        if (D == 2) return fmaf(dl[0][x], B[1][y], A[0][x] * dl[1][y]);
+        const int z = cz_of<D>(i) + 1;
+        return fmaf(dl[0][x] * B[1][y], B[2][z], fmaf(A[0][x] * dl[1][y], B[2][z], A[0][x] * A[1][y] * dl[2][z]));
+    }
+};
 
 // Slot of population i among the ones that carry the conservation
 // correction (rest, then -x, +x, -y, +y, -z, +z), or -1.

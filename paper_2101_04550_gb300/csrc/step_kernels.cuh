@@ -26,15 +26,16 @@ constexpr int kBlock = 256;
 
 // ---------------------------------------------------------------- two-pass
 // Pass 1: post-streaming moments of every node -> anomaly field q[a][cell]
-// (Eqs. density, momentum, Deviation).  Reads the populations only.
-template <int D, int ST, int PAR>
+// (Eqs. density, momentum, Deviation).  Reads the populations only.  BC: the
+// variant that honours walls (p.walls_y) and the body force (p.forced).
+template <int D, int ST, int PAR, bool BC = false>
 __global__ void __launch_bounds__(kBlock) k_anomaly(StepParams p)
 {
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
     const Node n = make_node<D>(p, cell);
     float g[Lat<D>::Q];
-    gather<D, ST, PAR>(p, n, g);
+    gather<D, ST, PAR>(p, n, g, BC && p.walls_y);
     float drho, j[3];
     moments<D>(p, g, drho, j);
     const float inv_rho = 1.0f / (p.rho_ref + drho);
@@ -67,8 +68,11 @@ __device__ __forceinline__ void moments_of(const StepParams& p, G&& gval, float&
 // Relaxation of one node toward the extended equilibrium with the
 // conservation correction of relax(), for populations read through gval(i)
 // (read twice, not kept in registers) and results handed to put(i, g'_i).
-// POLY selects the conventional second-order equilibrium instead.
-template <int D, bool POLY = false, typename G, typename P>
+// POLY selects the conventional second-order equilibrium instead.  BC adds
+// the body-force increment F_i (ForceIncrement) when p.forced is set; it is
+// kept out of the conservation moments, so the node gains exactly the
+// momentum rho g of the force.
+template <int D, bool POLY = false, bool BC = false, typename G, typename P>
 __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&& put, float drho,
                                                const float* j, const float* d)
 {
@@ -83,8 +87,11 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     }
     baseline_args<D>(p, u, pcorr, du, dP);
     const float om = p.omega;
+    const bool forced = BC && p.forced;
+    ForceIncrement<D> frc;
+    if (forced) frc.init(p, rho / om, u);
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-    float keep[2 * D + 1];
+    float keep[2 * D + 1], kf[2 * D + 1];
     auto relax_one = [&](int i, float geq) {
         const float gi = gval(i);
         const float dl = geq - gi;
@@ -96,21 +103,26 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
         if (cz_of<D>(i) == 1) ez += dl;
         if (cz_of<D>(i) == -1) ez -= dl;
         const int k = corrected_slot<D>(i);
-        if (k >= 0) keep[k] = geq;
-        else put(i, fmaf(om, dl, gi));
+        if (k >= 0) {
+            keep[k] = geq;
+            if (forced) kf[k] = frc(i);
+        } else {
+            put(i, fmaf(om, forced ? dl + frc(i) : dl, gi));
+        }
     };
     if (POLY) for_each_second_order<D>(p, drho, u, relax_one);
     else for_each_equilibrium<D>(p, drho, du, dP, relax_one);
+    auto inc = [&](int k, float v) { return forced ? v + kf[k] : v; };
     const float hx = 0.5f * ex, hy = 0.5f * ey;
-    put(I0, fmaf(om, (keep[0] - gval(I0)) - e0, gval(I0)));
-    put(I0 - 1, fmaf(om, (keep[1] - gval(I0 - 1)) + hx, gval(I0 - 1)));
-    put(I0 + 1, fmaf(om, (keep[2] - gval(I0 + 1)) - hx, gval(I0 + 1)));
-    put(I0 - 3, fmaf(om, (keep[3] - gval(I0 - 3)) + hy, gval(I0 - 3)));
-    put(I0 + 3, fmaf(om, (keep[4] - gval(I0 + 3)) - hy, gval(I0 + 3)));
+    put(I0, fmaf(om, inc(0, (keep[0] - gval(I0)) - e0), gval(I0)));
+    put(I0 - 1, fmaf(om, inc(1, (keep[1] - gval(I0 - 1)) + hx), gval(I0 - 1)));
+    put(I0 + 1, fmaf(om, inc(2, (keep[2] - gval(I0 + 1)) - hx), gval(I0 + 1)));
+    put(I0 - 3, fmaf(om, inc(3, (keep[3] - gval(I0 - 3)) + hy), gval(I0 - 3)));
+    put(I0 + 3, fmaf(om, inc(4, (keep[4] - gval(I0 + 3)) - hy), gval(I0 + 3)));
     if (D == 3) {
         const float hz = 0.5f * ez;
-        put(I0 - 9, fmaf(om, (keep[5] - gval(I0 - 9)) + hz, gval(I0 - 9)));
-        put(I0 + 9, fmaf(om, (keep[6] - gval(I0 + 9)) - hz, gval(I0 + 9)));
+        put(I0 - 9, fmaf(om, inc(5, (keep[5] - gval(I0 - 9)) + hz), gval(I0 - 9)));
+        put(I0 + 9, fmaf(om, inc(6, (keep[6] - gval(I0 + 9)) - hz), gval(I0 + 9)));
     }
 }
 
@@ -120,17 +132,20 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
 // (Eq. Paastar1), extended equilibrium, relaxation, write-back in place.
 // Populations are read back from the stage instead of being held in
 // registers, which keeps the register count low enough for 32 resident
-// warps per SM.
-template <int D, int ST, int PAR, int STRIDE = kBlock, bool POLY = false>
+// warps per SM.  BC: walls (bounce-back slots, and the anomaly's ghost value
+// beyond a wall is the negated value of the wall-adjacent node: Q~_yyy is odd
+// in u_y and u_y = 0 on the wall) and the body force.
+template <int D, int ST, int PAR, int STRIDE = kBlock, bool POLY = false, bool BC = false>
 __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, unsigned* col)
 {
     constexpr int Q = Lat<D>::Q;
     using S = Storage<ST>;
     const Node n = make_node<D>(p, cell);
+    const bool walls = BC && p.walls_y;
     unsigned halves = 0;  // bit i: population i sits in the upper half of its staged word
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int idx = read_slot<D>(n, p.N, i, PAR);
+        const int idx = read_slot<D>(n, p.N, i, PAR, walls);
         halves |= (unsigned)(idx & 1) << i;
         cp_async4(col + i * STRIDE, stage_src<ST>(p, idx));
     }
@@ -138,31 +153,40 @@ __device__ __forceinline__ void collide_staged(const StepParams& p, int cell, un
     if (p.eq_mode == 0) {
         const float* q = p.q;
         d[0] = (q[n.at(1, 0, 0)] - q[n.at(-1, 0, 0)]) * p.inv_2lam[0];
-        d[1] = (q[p.N + n.at(0, 1, 0)] - q[p.N + n.at(0, -1, 0)]) * p.inv_2lam[1];
+        const float* qy = q + p.N;
+        const float qyp = (walls && n.yhi) ? -qy[cell] : qy[n.at(0, 1, 0)];
+        const float qym = (walls && n.ylo) ? -qy[cell] : qy[n.at(0, -1, 0)];
+        d[1] = (qyp - qym) * p.inv_2lam[1];
         if (D == 3) d[2] = (q[2 * p.N + n.at(0, 0, 1)] - q[2 * p.N + n.at(0, 0, -1)]) * p.inv_2lam[2];
     }
     cp_async_wait_all();
-    auto gval = [&](int i) { return stage_value<ST>(p, ld_stage(col + i * STRIDE), (int)((halves >> i) & 1u), i); };
+    auto gval = [&](int i) {
+        const float v = stage_value<ST>(p, ld_stage(col + i * STRIDE), (int)((halves >> i) & 1u), i);
+        return (S::shifted && PAR == 1 && walls && read_bounced(n, i)) ? v + bounce_rebase<D>(p, i) : v;
+    };
     float drho, j[3];
     moments_of<D>(p, gval, drho, j);
     typename S::T* f = static_cast<typename S::T*>(p.f);
     const int cell_o = opaque(cell);
     auto put = [&](int i, float gn) {
-        const int slot = (PAR == 0) ? (Q - 1 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
+        const int slot = (PAR == 0) ? (Q - 1 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR, walls);
+        if (S::shifted && PAR == 1 && walls && write_bounced(n, i)) gn += bounce_rebase<D>(p, Q - 1 - i);
         S::store(f + slot, S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn));
     };
-    relax_streamed<D, POLY>(p, gval, put, drho, j, d);
+    relax_streamed<D, POLY, BC>(p, gval, put, drho, j, d);
 }
 
 // Pass 2 over every node: one node per thread, populations staged in shared
 // memory.  POLY: the conventional second-order equilibrium (no anomaly pass).
-template <int D, int ST, int PAR, bool POLY = false>
-__global__ void __launch_bounds__(kBlock, ELBM_COLLIDE_MIN_BLOCKS) k_collide(StepParams p)
+// BC: walls and body force (compiled for one resident block fewer: the force
+// terms need the registers).
+template <int D, int ST, int PAR, bool POLY = false, bool BC = false>
+__global__ void __launch_bounds__(kBlock, BC ? ELBM_COLLIDE_MIN_BLOCKS - 1 : ELBM_COLLIDE_MIN_BLOCKS) k_collide(StepParams p)
 {
     __shared__ unsigned stage[Lat<D>::Q * kBlock];
     const int cell = blockIdx.x * kBlock + threadIdx.x;
     if (cell >= p.N) return;
-    collide_staged<D, ST, PAR, kBlock, POLY>(p, cell, stage + threadIdx.x);
+    collide_staged<D, ST, PAR, kBlock, POLY, BC>(p, cell, stage + threadIdx.x);
 }
 
 template <int D>
@@ -171,6 +195,8 @@ cudaError_t step_two_pass_impl(const Solver& s, int parity, long long* launches)
     StepParams p;
     fill_params(s, p);
     p.parity = parity;
+    // walls and body force: the kernels of bounded_step.cuh (own translation units)
+    if (p.walls_y || p.forced) return step_bounded_impl<D>(s, parity, launches);
     const dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock));
     const dim3 cgrid = grid;
     ELBM_DISPATCH_STORAGE(s.storage, {
@@ -232,7 +258,7 @@ template <int D, int ST>
 __device__ __forceinline__ void gather_any(const StepParams& p, const Node& n, float* g)
 {
     if (p.parity == 0) gather<D, ST, 0>(p, n, g);
-    else gather<D, ST, 1>(p, n, g);
+    else gather<D, ST, 1>(p, n, g, p.walls_y != 0);
 }
 
 // rho and u of every node (Eqs. density, momentum) with the step kernels'
@@ -276,8 +302,11 @@ __device__ __forceinline__ double load_f64(const StepParams& p, const Node& n, i
 {
     using S = Storage<ST>;
     const typename S::T* f = static_cast<const typename S::T*>(p.f);
-    const float v = S::load(f + read_slot<D>(n, p.N, i, p.parity));
-    return S::shifted ? (double)v + (double)p.bw[i] * (double)p.rho_ref : (double)v;
+    const bool walls = p.walls_y != 0;
+    const float v = S::load(f + read_slot<D>(n, p.N, i, p.parity, walls));
+    // a bounced slot holds population opp(i), stored against its own baseline
+    const int b = (p.parity == 1 && walls && read_bounced(n, i)) ? Lat<D>::Q - 1 - i : i;
+    return S::shifted ? (double)v + (double)p.bw[b] * (double)p.rho_ref : (double)v;
 }
 
 // Unshifted post-streaming populations f_i = g_i + w_i rho_ref, layout f[i][cell].
@@ -402,7 +431,11 @@ __device__ __forceinline__ void block_reduce(double* acc, double* out)
 }
 
 // Stage 2: per-block FP64 partial sums (grid-stride over nodes); vorticity and
-// d_x u_x by central differences with node spacing lam.
+// d_x u_x by central differences with node spacing lam.  With walls the
+// velocity beyond a wall is the negated value of the wall-adjacent node
+// (no slip half-way between the nodes), and the wall-normal gradient of u_x
+// at each wall node comes from the quadratic through the wall (u = 0, a
+// distance lam_y/2 away) and the first two nodes: (9 u_x(1st) - u_x(2nd)) / (3 lam_y).
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* mom, double* partials)
 {
@@ -421,11 +454,21 @@ __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* m
         const float u0 = ux[cell], u1 = uy[cell], u2 = uz[cell];
         const float uu = u0 * u0 + u1 * u1 + u2 * u2;
         const bool finite = isfinite(r) && isfinite(uu);
+        const bool walls = p.walls_y != 0;
+        auto dy = [&](const float* v) {
+            const float up = (walls && n.yhi) ? -v[cell] : v[n.at(0, 1, 0)];
+            const float dn = (walls && n.ylo) ? -v[cell] : v[n.at(0, -1, 0)];
+            return (up - dn) * iy;
+        };
         const float dxuy = (uy[n.at(1, 0, 0)] - uy[n.at(-1, 0, 0)]) * ix;
-        const float dyux = (ux[n.at(0, 1, 0)] - ux[n.at(0, -1, 0)]) * iy;
+        const float dyux = dy(ux);
         float w2 = (dxuy - dyux) * (dxuy - dyux);
+        if (walls && (n.ylo || n.yhi)) {
+            const float second = n.ylo ? ux[n.at(0, 1, 0)] : ux[n.at(0, -1, 0)];
+            acc[12] += (double)((9.0f * u0 - second) * (1.0f / (3.0f * p.lam[1])));
+        }
         if (D == 3) {
-            const float dyuz = (uz[n.at(0, 1, 0)] - uz[n.at(0, -1, 0)]) * iy;
+            const float dyuz = dy(uz);
             const float dzuy = (uy[n.at(0, 0, 1)] - uy[n.at(0, 0, -1)]) * iz;
             const float dzux = (ux[n.at(0, 0, 1)] - ux[n.at(0, 0, -1)]) * iz;
             const float dxuz = (uz[n.at(1, 0, 0)] - uz[n.at(-1, 0, 0)]) * ix;

@@ -21,13 +21,13 @@ DTYPE_F32, DTYPE_F64 = 0, 1
 OPT_EQUILIBRIUM, OPT_KERNEL, OPT_RHO_REF = 1, 2, 3
 OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z, OPT_WALLS_Y = 4, 5, 6, 7
 OPT_U_REF_X, OPT_U_REF_Y, OPT_U_REF_Z, OPT_U_REF_AUTO = 8, 9, 10, 11
-NRED = 12
+NRED = 13
 ERRORS = {0: "OK", -1: "ARG", -2: "UNREALIZABLE", -3: "OOM", -4: "CUDA", -5: "NONFINITE",
           -6: "TIMEOUT", -7: "STATE"}
 STORAGE_NAMES = {"f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT, "f32s": F32_SHIFT}
 STORAGE_BYTES = {F32: 4, F16_SHIFT: 2, BF16_SHIFT: 2, F32_SHIFT: 4}
 RED_NAMES = ["mass", "mom_x", "mom_y", "mom_z", "rho_u2", "u2", "curl2", "dxux2", "ux2", "fmin",
-             "nonfinite", "umax"]
+             "nonfinite", "umax", "wall_dudn"]
 
 _lock = threading.Lock()
 _lib = None
@@ -118,10 +118,12 @@ def _buffer(a, dtype):
 
 
 class Solver:
-    """One periodic grid on the GPU, advanced by the extended LBGK step."""
+    """One grid on the GPU, advanced by the extended LBGK step: periodic, or
+    with half-way bounce-back walls in y (``walls_y``) and a constant body
+    force ``force`` = (g_x, g_y, g_z)."""
 
     def __init__(self, lattice, n, stretch=(1.0, 1.0, 1.0), T=1.0 / 3.0, nu=0.01, storage=F32,
-                 stream=None, kernel=0, equilibrium=0, u_ref=None):
+                 stream=None, kernel=0, equilibrium=0, u_ref=None, walls_y=False, force=None):
         L = load()
         self.lattice = lattice
         self.D = 2 if lattice == D2Q9 else 3
@@ -152,6 +154,11 @@ class Solver:
             self.set_option(OPT_KERNEL, kernel)
         if equilibrium:
             self.set_option(OPT_EQUILIBRIUM, equilibrium)
+        if walls_y:
+            self.set_option(OPT_WALLS_Y, 1)
+        if force is not None:
+            for a, v in enumerate(force):
+                self.set_option(OPT_FORCE_X + a, float(v))
         if isinstance(u_ref, str) and u_ref == "mean":
             self.set_option(OPT_U_REF_AUTO, 1)
         elif u_ref is not None:
