@@ -354,37 +354,4 @@ bool single_fast_ok(const Solver& s)
 
 inline size_t single_pass_smem() { return sizeof(SingleSmem); }
 
-// One single-pass step from s.f into dst (D3Q27 only; the caller swaps the arrays).
-template <int D>
-cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
-{
-    if constexpr (D != 3) {
-        (void)s;
-        (void)dst;
-        (void)launches;
-        return cudaErrorNotSupported;
-    } else {
-        StepParams p;
-        fill_params(s, p);
-        p.parity = 0;
-        const dim3 grid((unsigned)((s.nx + kTileX - 1) / kTileX), (unsigned)((s.ny + kTileY - 1) / kTileY),
-                        (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
-        const size_t smem = sizeof(SingleSmem);
-        cudaError_t e = cudaSuccess;
-        ELBM_DISPATCH_STORAGE(s.storage, {
-            if (single_fast_ok<ST>(s)) {
-                const size_t fsmem = sizeof(FastSmem<ST>);
-                e = cudaFuncSetAttribute(k_single_pass_fast<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                if (e == cudaSuccess) k_single_pass_fast<ST><<<grid, kBlock, fsmem, s.stream>>>(p, dst);
-            } else {
-                e = cudaFuncSetAttribute(k_single_pass<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e == cudaSuccess) k_single_pass<ST><<<grid, kBlock, smem, s.stream>>>(p, dst);
-            }
-        });
-        if (e != cudaSuccess) return e;
-        ++*launches;
-        return cudaGetLastError();
-    }
-}
-
 }  // namespace elbm

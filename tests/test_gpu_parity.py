@@ -175,8 +175,9 @@ def test_d3q27_minimum_grid():
 # ---------------------------------------------------- kernels and state
 @pytest.mark.parametrize("lattice,n", [(elbm.D3Q27, (64, 64, 48)), (elbm.D3Q27, (40, 24, 3)),
                                        (elbm.D3Q27, (5, 3, 70)), (elbm.D3Q27, (70, 20, 33)),
+                                       (elbm.D3Q27, (64, 8, 3)), (elbm.D3Q27, (32, 16, 35)),
                                        (elbm.D2Q9, (300, 700)), (elbm.D2Q9, (33, 5))])
-@pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT, elbm.F32_SHIFT])
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT, elbm.F32_SHIFT, elbm.BF16_SHIFT])
 def test_kernel_forms_agree_bitwise(lattice, n, storage):
     """The two-pass, graph-pipelined and (D3Q27) single-pass forms evaluate the same
     per-node arithmetic, so the states agree bit for bit, across launches of
