@@ -43,7 +43,7 @@ CHANNEL.update(nu=CHANNEL["u_tau"] * 64 / 180.0, g=CHANNEL["u_tau"] ** 2 / 64)
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_NAMES = {0: "two-pass", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
 KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range",
-                   3: "k_single_pass_fast"}
+                   3: "k_single_pass_tmem"}
 # ncu DRAM bytes (read + write) of one step of the timed kernel form, keyed by
 # the hash of the kernel sources they were measured on, the storage and the form.
 # 339 B/node measured at 192^3 (profiles/k_anomaly_k_collide_d3q27_hit192_f32.md), scaled
@@ -251,7 +251,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
-    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--kernel", type=int, default=3, choices=[0, 1, 2, 3],
                     help="0 automatic, 1 two-pass in place, 2 graph-pipelined in place, 3 single pass (two arrays)")
     ap.add_argument("--reduce-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -370,8 +370,8 @@ def main():
     # ---- variants (same workload, other storage / kernel form) ----------
     variants = {}
     if not args.no_variants and rank == 0:
-        for name, st, ker in (("f16_shift_two_pass", elbm.F16_SHIFT, 1), ("f16_shift_single_pass", elbm.F16_SHIFT, 3),
-                              ("f32_shift_single_pass", elbm.F32_SHIFT, 3), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2)):
+        for name, st, ker in (("f32_shift_two_pass", elbm.F32_SHIFT, 1), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2),
+                              ("f16_shift_single_pass", elbm.F16_SHIFT, 3), ("f16_shift_two_pass", elbm.F16_SHIFT, 1)):
             sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every)
             sv.close()
             nsteps = min(args.steps, 200)

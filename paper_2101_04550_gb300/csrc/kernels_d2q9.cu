@@ -1,6 +1,6 @@
 // Instantiation of the step kernels and their launchers for the D2Q9 lattice.
 #include "step_kernels.cuh"
-#include "single_pass_tma.cuh"
+#include "single_pass_tmem.cuh"
 #include "graph_step.cuh"
 #include "batch.cuh"
 

@@ -86,6 +86,70 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// ------------------------------------------------ tensor memory (TMEM)
+// Tensor memory holds 128 lanes x 512 columns of 32 bits per SM; warp w of a
+// CTA reaches lanes 32 (w % 4) .. 32 (w % 4) + 31 (its lane quarter), so CTAs
+// that use it are whole warpgroups.
+__device__ __forceinline__ void tmem_alloc(uint32_t smem_dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_dst), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 27 floats of this thread into columns t .. t+26 of its lane (x16 + x8 + x2 + x1).
+__device__ __forceinline__ void tmem_store27(uint32_t t, const float* v)
+{
+#define ELBM_R(k) "r"(__float_as_uint(v[k]))
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(t),
+        ELBM_R(0), ELBM_R(1), ELBM_R(2), ELBM_R(3), ELBM_R(4), ELBM_R(5), ELBM_R(6), ELBM_R(7), ELBM_R(8), ELBM_R(9),
+        ELBM_R(10), ELBM_R(11), ELBM_R(12), ELBM_R(13), ELBM_R(14), ELBM_R(15)
+        : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(t + 16),
+                 ELBM_R(16), ELBM_R(17), ELBM_R(18), ELBM_R(19), ELBM_R(20), ELBM_R(21), ELBM_R(22), ELBM_R(23)
+                 : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(t + 24), ELBM_R(24), ELBM_R(25)
+                 : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(t + 26), ELBM_R(26) : "memory");
+#undef ELBM_R
+}
+// ... and back (waits for the loads before returning the values).
+__device__ __forceinline__ void tmem_load27(uint32_t t, float* v)
+{
+    uint32_t r[27];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(t)
+        : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                   "=r"(r[23])
+                 : "r"(t + 16)
+                 : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[24]), "=r"(r[25]) : "r"(t + 24)
+                 : "memory");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r[26]) : "r"(t + 26) : "memory");
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 27; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory layout (byte offsets from a 128-byte aligned base).  TMA
 // destinations start on 128-byte boundaries.
 template <int ST>
@@ -119,7 +183,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     using S = Storage<ST>;
     using T = typename S::T;
     using L = TmaLayout<ST>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t sbase = (raw_addr + 127u) & ~127u;
     unsigned char* base = smem_raw + (sbase - raw_addr);
@@ -314,8 +378,8 @@ bool single_tma_ok(const Solver& s, const void* src, const void* dst)
 }
 
 // Tensor maps of one population array: dims (x, y, z, population), boxes of
-// the tile (32 x 8 x 1 x 27) and of one ring row (32 x 1 x 1 x 27).
-cudaError_t encode_population_maps(const Solver& s, const void* f, CUtensorMap* tile, CUtensorMap* row);
+// the tile (32 x tile_y x 1 x 27) and of one ring row (32 x 1 x 1 x 27).
+cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row);
 
 template <int ST>
 cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, bool* launched)
@@ -323,7 +387,7 @@ cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, b
     *launched = false;
     if (!single_tma_ok<ST>(s, p.f, dst)) return cudaSuccess;
     CUtensorMap tm_tile, tm_row;
-    cudaError_t e = encode_population_maps(s, p.f, &tm_tile, &tm_row);
+    cudaError_t e = encode_population_maps(s, p.f, kTileY, &tm_tile, &tm_row);
     if (e != cudaSuccess) return cudaSuccess;  // no TMA: the caller takes another single-pass kernel
     const int smem = TmaLayout<ST>::bytes;
     e = cudaFuncSetAttribute(k_single_pass_tma<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -333,46 +397,6 @@ cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, b
     k_single_pass_tma<ST><<<grid, kTmaThreads, smem, s.stream>>>(tm_tile, tm_row, p, dst);
     *launched = true;
     return cudaGetLastError();
-}
-
-// One single-pass step from s.f into dst (D3Q27 only; the caller swaps the arrays):
-// the TMA-fed kernel where the geometry allows, else the cp.async-staged ones.
-template <int D>
-cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
-{
-    if constexpr (D != 3) {
-        (void)s;
-        (void)dst;
-        (void)launches;
-        return cudaErrorNotSupported;
-    } else {
-        StepParams p;
-        fill_params(s, p);
-        p.parity = 0;
-        const dim3 grid((unsigned)((s.nx + kTileX - 1) / kTileX), (unsigned)((s.ny + kTileY - 1) / kTileY),
-                        (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
-        const size_t smem = sizeof(SingleSmem);
-        cudaError_t e = cudaSuccess;
-        ELBM_DISPATCH_STORAGE(s.storage, {
-            bool done = false;
-            e = launch_single_tma<ST>(s, p, dst, &done);
-            if (e != cudaSuccess || done) {
-                if (e == cudaSuccess) ++*launches;
-                return e;
-            }
-            if (single_fast_ok<ST>(s)) {
-                const size_t fsmem = sizeof(FastSmem<ST>);
-                e = cudaFuncSetAttribute(k_single_pass_fast<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-                if (e == cudaSuccess) k_single_pass_fast<ST><<<grid, kBlock, fsmem, s.stream>>>(p, dst);
-            } else {
-                e = cudaFuncSetAttribute(k_single_pass<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e == cudaSuccess) k_single_pass<ST><<<grid, kBlock, smem, s.stream>>>(p, dst);
-            }
-        });
-        if (e != cudaSuccess) return e;
-        ++*launches;
-        return cudaGetLastError();
-    }
 }
 
 }  // namespace elbm

@@ -31,16 +31,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }  // namespace
 
 // Layout f[i][z][y][x] as a 4-D tensor (x, y, z, i) of 4- or 2-byte elements;
-// boxes of 32 x 8 x 1 x 27 (the tile of one plane) and 32 x 1 x 1 x 27 (one
+// boxes of 32 x tile_y x 1 x 27 (the tile of one plane) and 32 x 1 x 1 x 27 (one
 // ring row).  Strides are multiples of 16 bytes when nx * element size is.
-cudaError_t encode_population_maps(const Solver& s, const void* f, CUtensorMap* tile, CUtensorMap* row)
+cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || s.D != 3) return cudaErrorNotSupported;
     const cuuint64_t es = storage_bytes(s.storage);
     const cuuint64_t dims[4] = {(cuuint64_t)s.nx, (cuuint64_t)s.ny, (cuuint64_t)s.nz, 27};
     const cuuint64_t strides[3] = {s.nx * es, (cuuint64_t)s.nx * s.ny * es, (cuuint64_t)s.N * es};
-    const cuuint32_t box_tile[4] = {32, 8, 1, 27}, box_row[4] = {32, 1, 1, 27}, unit[4] = {1, 1, 1, 1};
+    const cuuint32_t box_tile[4] = {32, (cuuint32_t)tile_y, 1, 27}, box_row[4] = {32, 1, 1, 27}, unit[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     for (int k = 0; k < 2; ++k) {
         CUresult r = fn(k == 0 ? tile : row, dt, 4, const_cast<void*>(f), dims, strides, k == 0 ? box_tile : box_row,
