@@ -46,9 +46,11 @@ KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_ano
                    3: "k_single_pass_tmem"}
 # ncu DRAM bytes (read + write) of one step of the timed kernel form, keyed by
 # the hash of the kernel sources they were measured on, the storage and the form.
-# 339 B/node measured at 192^3 (profiles/k_anomaly_k_collide_d3q27_hit192_f32.md), scaled
-# to the 256^3 step: 339.1 * 256^3 bytes.
-MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47", "f32s", 1): 5.689e9}
+# Two-pass: 339 B/node measured at 192^3 (profiles/k_anomaly_k_collide_d3q27_hit192_f32.md),
+# scaled to the 256^3 step: 339.1 * 256^3 bytes.
+MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47", "f32s", 1): 5.689e9,
+                    # 218.5 B/node measured at 192^3 (profiles/k_single_pass_tmem_d3q27_hit192_f32.md) x 256^3
+                    ("ea6c7fce23e1af60", "f32s", 3): 3.666e9}
 
 
 def kernel_source_hash() -> str:
