@@ -78,7 +78,12 @@ extern "C" {
  *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide
  *       kernels, so that the collide kernels re-read populations from L2;
  *   3 = single pass with a second population array (D3Q27 only): every block
- *       recomputes the anomaly around its tile and reads the populations once. */
+ *       recomputes the anomaly around its tile and reads the populations once
+ *       (TMA-fed, populations parked in tensor memory, when nx is a multiple
+ *       of 32 and ny of 16; 32 x 8 TMA tiles when ny is a multiple of 8;
+ *       cp.async-staged otherwise).  Setting it allocates the second array.
+ *   The second-order equilibrium, walls and the body force always run in the
+ *   two-pass form, whatever form is set. */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3

@@ -25,8 +25,13 @@
  * 27eqext), BGK relaxation and streaming (Eq. LBGK).  Populations are kept in
  * two arrays (read one, write the other).
  *
- * Parity of the body-force and wall options is unpinned by the paper (it gives
- * neither scheme); they follow the readings listed in the design notes.
+ * The paper gives neither a wall scheme nor a forcing scheme for its channel
+ * (Sec. III.E); the wall and body-force options follow stated readings
+ * (half-way bounce-back with a negated ghost anomaly; exact-difference
+ * forcing) and are pinned by a closed form (uniform acceleration), exact
+ * conservation, mirror symmetry and the steady Poiseuille parabola.
+ *
+ * Test infrastructure: the GPU library never calls this code.
  */
 #include <math.h>
 #include <stdlib.h>
