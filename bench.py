@@ -233,14 +233,16 @@ def serve_arm(args):
     warm = serve.make_trace(2, rate=1000.0, seed=99, steps=20, sizes=(32,))
     serve.Server(stream=stream).run(warm, mode="batched")
     serve.Server(stream=stream).run(warm, mode="plain")
-    batched = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream).run(trace, mode="batched")
+    batched = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt").run(trace, mode="batched")
+    batched_fifo = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream).run(trace, mode="batched")
     plain = serve.Server(stream=stream).run(trace, mode="plain")
     line = {"metric": "served aggregate MLUPS", "value": batched["aggregate_MLUPS"], "unit": "MLUPS",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32 compute, f32/f16 shifted storage",
             "data": "synthetic", "config": {"workload": "served mix: Poisson arrivals 20/s of D3Q27 shear-wave "
                                                         "and Taylor-Green solves, 2000 steps each",
                                             "requests": len(trace), "hbm_budget_GiB": 8, "chunk_steps": 100},
-            "batched": batched, "plain": plain,
+            "batched": batched, "batched_fifo": batched_fifo, "plain": plain,
+            "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 4 Mi nodes",
             "speedup_vs_plain": batched["aggregate_MLUPS"] / plain["aggregate_MLUPS"]}
     print(json.dumps(line), flush=True)
     return 0

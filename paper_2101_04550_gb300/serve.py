@@ -92,20 +92,47 @@ def initial_field(req: Request):
     return rho, u
 
 
+@dataclasses.dataclass
+class _Slot:
+    """A resident request: its solver, the steps it still has to run, when it
+    was admitted, and whether its solver is currently a member of its batch."""
+    req: Request
+    solver: object
+    left: int
+    t_admit: float
+    in_batch: bool = False
+
+    @property
+    def key(self):
+        return (self.req.lattice, self.req.storage)
+
+
 class Server:
     """Continuous-batching server over one GPU stream.
 
-    hbm_budget   bytes of populations + anomaly fields that may be resident
-    chunk_steps  steps between admission points
-    max_active   resident requests at most
-    clock        callable giving seconds (wall clock by default)
+    hbm_budget        bytes of populations + anomaly fields that may be resident
+    chunk_steps       steps between admission points
+    max_active        resident requests at most
+    policy            "fifo": admit in arrival order and advance every resident
+                      request each chunk; "srpt": admit the smallest waiting
+                      request that fits, and each chunk advance the resident
+                      requests with the least remaining work (cells x steps
+                      left) until step_floor_nodes nodes are in the batch, so
+                      that small solves are not held back by large ones while
+                      the GPU stays full
+    step_floor_nodes  nodes per batched step below which "srpt" adds more requests
+    clock             callable giving seconds (wall clock by default)
     """
 
     def __init__(self, hbm_budget=8 << 30, chunk_steps=100, max_active=64, clock=time.perf_counter,
-                 stream=None, sleep=time.sleep):
+                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=4 << 20):
+        if policy not in ("fifo", "srpt"):
+            raise ValueError("policy must be 'fifo' or 'srpt'")
         self.hbm_budget = int(hbm_budget)
         self.chunk_steps = int(chunk_steps)
         self.max_active = int(max_active)
+        self.policy = policy
+        self.step_floor_nodes = int(step_floor_nodes)
         self.clock = clock
         self.sleep = sleep
         self.stream = stream
@@ -127,6 +154,34 @@ class Server:
         self.results[req.rid] = {"u": u, "arrival": req.arrival, "admitted": t_admit, "done": t_done,
                                  "latency": t_done - req.arrival, "cells": req.cells, "steps": req.steps}
 
+    def _next_waiting(self, queue, used, kinds, n_active):
+        """Index in the queue of the request to admit next, or None."""
+        if n_active >= self.max_active:
+            return None
+        order = range(len(queue))
+        if self.policy == "srpt":
+            order = sorted(order, key=lambda i: (queue[i].cells * queue[i].steps, queue[i].arrival))
+        for i in order:
+            req = queue[i]
+            fits = used + req.device_bytes() <= self.hbm_budget and kinds[(req.lattice, req.storage)] < BATCH_MAX
+            if fits:
+                return i
+            if self.policy == "fifo":
+                return None  # strict arrival order
+        return None
+
+    def _stepping(self, active):
+        """The resident requests to advance in this chunk."""
+        if self.policy == "fifo":
+            return list(active)
+        chosen, nodes = [], 0
+        for a in sorted(active, key=lambda a: (a.req.cells * a.left, a.req.arrival)):
+            chosen.append(a)
+            nodes += a.req.cells
+            if nodes >= self.step_floor_nodes:
+                break
+        return chosen
+
     def run(self, trace, mode="batched"):
         """Serve a trace; returns the summary (latencies, makespan, throughput)."""
         self.results = {}
@@ -145,55 +200,68 @@ class Server:
             return self.summary(trace)
 
         pending = collections.deque(trace)
-        queue = collections.deque()
-        active = []           # [req, solver, steps_left, t_admit(, batch key once joined)]
+        queue = []
+        active = []           # _Slot of every resident request
         used = 0
-        batches = {}          # (lattice, storage) -> Batch of the resident requests of that kind
+        batches = {}          # (lattice, storage) -> Batch of the stepping members of that kind
         while pending or queue or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
-            kinds = collections.Counter((a[0].lattice, a[0].storage) for a in active)
-            while (queue and len(active) < self.max_active and used + queue[0].device_bytes() <= self.hbm_budget
-                   and kinds[(queue[0].lattice, queue[0].storage)] < BATCH_MAX):
-                req = queue[0]
+            kinds = collections.Counter(a.key for a in active)
+            while queue:
+                i = self._next_waiting(queue, used, kinds, len(active))
+                if i is None:
+                    break
+                req = queue[i]
                 try:
                     solver = self._start(req)
                 except elbm.ElbmError as err:
                     if err.code != -3 or not active:  # out of memory with nothing to wait for: give up on it
-                        queue.popleft()
+                        queue.pop(i)
                         self.failed[req.rid] = str(err)
                     break  # out of memory while others run: retry once some finish
-                queue.popleft()
+                queue.pop(i)
                 used += req.device_bytes()
                 kinds[(req.lattice, req.storage)] += 1
-                active.append([req, solver, req.steps, self.clock() - t0])
+                active.append(_Slot(req, solver, req.steps, self.clock() - t0))
             if not active:
-                if queue and used + queue[0].device_bytes() > self.hbm_budget:
-                    req = queue.popleft()  # larger than the whole budget
+                if queue and all(used + r.device_bytes() > self.hbm_budget for r in queue):
+                    req = min(queue, key=lambda r: r.arrival)  # larger than the whole budget
+                    queue.remove(req)
                     self.failed[req.rid] = f"needs {req.device_bytes()} bytes, budget {self.hbm_budget}"
                     continue
                 if pending and not queue:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
-            chunk = min(self.chunk_steps, min(a[2] for a in active))
-            for a in active:  # newly admitted requests join their group's batch
-                key = (a[0].lattice, a[0].storage)
-                if len(a) == 4:
-                    if key not in batches:
-                        batches[key] = elbm.Batch([a[1]])
+            stepping = self._stepping(active)
+            chosen = set(id(a) for a in stepping)
+            # batch membership follows the stepping set
+            for a in active:
+                if a.in_batch and id(a) not in chosen:
+                    batches[a.key].remove(a.solver)
+                    a.in_batch = False
+            for key in [k for k, b in batches.items() if len(b) == 0]:
+                batches.pop(key).close()
+            for a in stepping:
+                if not a.in_batch:
+                    if a.key not in batches:
+                        batches[a.key] = elbm.Batch([a.solver])
                     else:
-                        batches[key].add(a[1])
-                    a.append(key)
+                        batches[a.key].add(a.solver)
+                    a.in_batch = True
+            chunk = min(self.chunk_steps, min(a.left for a in stepping))
             for b in batches.values():
                 b.step(chunk)
             still = []
             for a in active:
-                a[2] -= chunk
-                if a[2] == 0:
-                    batches[a[4]].remove(a[1])
-                    self._finish(a[0], a[1], t0, a[3])
-                    used -= a[0].device_bytes()
+                if id(a) in chosen:
+                    a.left -= chunk
+                if a.left == 0:
+                    batches[a.key].remove(a.solver)
+                    a.in_batch = False
+                    self._finish(a.req, a.solver, t0, a.t_admit)
+                    used -= a.req.device_bytes()
                 else:
                     still.append(a)
             active = still

@@ -19,12 +19,16 @@ def small_trace():
     return trace
 
 
-def test_mix_equals_alone_and_oracle():
+@pytest.mark.parametrize("policy", ["fifo", "srpt"])
+def test_mix_equals_alone_and_oracle(policy):
+    """With either policy (the "srpt" one changes the batch membership from
+    chunk to chunk) every request ends bit-identical to its solo run."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     trace = small_trace()
     stream = torch.cuda.current_stream()
-    mixed = serve.Server(hbm_budget=3 * max(r.device_bytes() for r in trace), chunk_steps=20, stream=stream)
+    mixed = serve.Server(hbm_budget=3 * max(r.device_bytes() for r in trace), chunk_steps=20, stream=stream,
+                         policy=policy, step_floor_nodes=2 * 24 ** 3)
     s_mix = mixed.run(trace, mode="batched")
     alone = serve.Server(stream=stream)
     s_alone = alone.run(trace, mode="plain")

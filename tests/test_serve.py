@@ -1,6 +1,8 @@
 """Host-side logic of the serving loop, with fake solvers (no GPU): trace
 generation, HBM-budget admission, continuous batching (requests join while
 others are mid-flight), and an allocation failure injected on the host."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -83,9 +85,10 @@ class World:
         return FakeBatch
 
 
-def serve_fake(monkeypatch, trace, budget, fail_rids=(), mode="batched", chunk=50):
+def serve_fake(monkeypatch, trace, budget, fail_rids=(), mode="batched", chunk=50, policy="fifo", floor=4 << 20):
     clock = FakeClock()
-    server = serve.Server(hbm_budget=budget, chunk_steps=chunk, clock=clock, sleep=clock.sleep)
+    server = serve.Server(hbm_budget=budget, chunk_steps=chunk, clock=clock, sleep=clock.sleep, policy=policy,
+                          step_floor_nodes=floor)
     world = World(clock, fail_rids)
     orig_start = server._start
 
@@ -143,3 +146,34 @@ def test_plain_mode_serves_in_order(monkeypatch):
     server, summary, world = serve_fake(monkeypatch, trace, budget=1 << 40, mode="plain")
     done = [server.results[r.rid]["done"] for r in trace]
     assert done == sorted(done) and summary["served"] == 8
+
+
+@pytest.mark.parametrize("policy", ["fifo", "srpt"])
+def test_every_policy_runs_every_request_exactly(monkeypatch, policy):
+    trace = serve.make_trace(40, seed=8, steps=300, rate=100.0)
+    budget = 6 * max(r.device_bytes() for r in trace)
+    server, summary, world = serve_fake(monkeypatch, trace, budget, policy=policy, floor=1 << 20)
+    assert summary["served"] == 40 and world.peak_bytes <= budget
+    for r in trace:
+        assert server.results[r.rid]["u"][0] == 300
+
+
+def test_srpt_lets_small_requests_pass_a_large_one(monkeypatch):
+    """A 128^3 request arrives first, then ten 32^3 ones: with "srpt" most small
+    ones finish before it (the large one fills in whenever the small ones fall
+    short of the node floor), and the median latency drops below "fifo"'s."""
+    base = serve.make_trace(11, seed=9, steps=400, rate=1000.0)
+    big = dataclasses.replace(base[0], n=(128, 128, 128), arrival=0.0, rid=0)
+    small = [dataclasses.replace(r, n=(32, 32, 32), arrival=1e-3 * (k + 1), rid=k + 1) for k, r in enumerate(base[1:])]
+    trace = [big] + small
+    floor = 3 * 32 ** 3
+    server, summary, world = serve_fake(monkeypatch, trace, budget=1 << 40, policy="srpt", floor=floor)
+    done = {rid: server.results[rid]["done"] for rid in server.results}
+    assert sum(done[k] < done[0] for k in range(1, 11)) >= 8
+    cells = {r.rid: r.cells for r in trace}
+    for ids in world.batch_log:
+        stepped = sum(cells[i] for i in ids)
+        # the floor is met, or everything resident is being stepped
+        assert stepped >= floor or len(ids) == len(set(ids))
+    fifo_server, fifo_summary, _ = serve_fake(monkeypatch, trace, budget=1 << 40, policy="fifo")
+    assert summary["p50_latency_s"] < fifo_summary["p50_latency_s"]
