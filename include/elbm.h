@@ -259,6 +259,21 @@ int elbm_get_u_ref(const elbm_solver* s, double* out);
 int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const double* stretch, double T,
                       double nu, float* f, int nsteps, void* stream);
 
+/*
+ * Self-test of the device-side failure detection (not part of the paper's
+ * method).  The TMA-fed single-pass kernels wait on mbarriers; each wait is
+ * bounded in time and, when it gives up, sets ELBM_ERR_TIMEOUT in the solver's
+ * status word (read by elbm_sync, elbm_moments, elbm_get_populations and
+ * elbm_reduce) instead of hanging.  This call runs that same bounded wait on
+ * a barrier phase that never completes, with a bound of limit_ms (1..2000)
+ * milliseconds, on `stream` (NULL: the legacy default stream), and waits for
+ * it.  Returns ELBM_ERR_TIMEOUT when the wait gave up as designed (the
+ * expected result); ELBM_ERR_ARG for a bound out of range; ELBM_ERR_CUDA on a
+ * CUDA error; ELBM_ERR_STATE if no timeout was reported.  The device stays
+ * usable afterwards.
+ */
+int elbm_selftest_wait_timeout(int limit_ms, void* stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* elbm_last_error(void);
 

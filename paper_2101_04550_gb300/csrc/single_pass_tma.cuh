@@ -76,6 +76,37 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint32_t bar)
 {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
+// Bounded wait for the completion of phase `parity` of an mbarrier: gives up
+// after limit_ns (read from %globaltimer), or as soon as another thread of
+// the block has given up (*abort_flag); the first thread to give up raises
+// the flag and stores ELBM_ERR_TIMEOUT in the status word.  Returns true once
+// the phase has completed.
+__device__ __forceinline__ bool bounded_wait(uint32_t bar, unsigned parity, volatile int* abort_flag, int* status,
+                                             unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned n = 1;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 63) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                if (!*abort_flag) {
+                    *abort_flag = 1;
+                    atomicExch(status, ELBM_ERR_TIMEOUT);
+                }
+                return false;
+            }
+        }
+    }
+}
+// The same bound, for draining copies in flight (ignores the abort flag).
+__device__ __forceinline__ void bounded_drain(uint32_t bar, unsigned parity, unsigned long long limit_ns)
+{
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < limit_ns) {}
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint32_t bar)
 {
@@ -216,32 +247,9 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     }
     __syncthreads();
 
-    auto give_up = [&]() {
-        if (!*abort_flag) {
-            *abort_flag = 1;
-            atomicExch(p.status, ELBM_ERR_TIMEOUT);
-        }
-    };
-    // bounded in time: 2 s, or as soon as another thread of the block gave up
-    auto wait = [&](uint32_t bar, unsigned parity) -> bool {
-        if (mbar_try_wait(bar, parity)) return true;
-        const unsigned long long t0 = globaltimer_ns();
-        for (unsigned n = 1;; ++n) {
-            if (mbar_try_wait(bar, parity)) return true;
-            if ((n & 63) == 0) {
-                if (*abort_flag) return false;
-                if (globaltimer_ns() - t0 > kTmaWaitNs) {
-                    give_up();
-                    return false;
-                }
-            }
-        }
-    };
-    // the same bound, for draining the copies in flight (ignores the abort flag)
-    auto drain = [&](uint32_t bar, unsigned parity) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < kTmaWaitNs) {}
-    };
+    // bounded in time (kTmaWaitNs), or as soon as another thread of the block gave up
+    auto wait = [&](uint32_t bar, unsigned parity) { return bounded_wait(bar, parity, abort_flag, p.status, kTmaWaitNs); };
+    auto drain = [&](uint32_t bar, unsigned parity) { bounded_drain(bar, parity, kTmaWaitNs); };
     auto plane_of = [&](int k) { return wrapi(z0 - 1 + k, p.nz); };
 
     if (warp == kBlock / 32) {

@@ -106,30 +106,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     tmem_fence_after_sync();
     const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(base + L::off_tmem);
 
-    auto give_up = [&]() {
-        if (!*abort_flag) {
-            *abort_flag = 1;
-            atomicExch(p.status, ELBM_ERR_TIMEOUT);
-        }
-    };
-    auto wait = [&](uint32_t bar, unsigned parity) -> bool {
-        if (mbar_try_wait(bar, parity)) return true;
-        const unsigned long long t0 = globaltimer_ns();
-        for (unsigned n = 1;; ++n) {
-            if (mbar_try_wait(bar, parity)) return true;
-            if ((n & 63) == 0) {
-                if (*abort_flag) return false;
-                if (globaltimer_ns() - t0 > kTmaWaitNs) {
-                    give_up();
-                    return false;
-                }
-            }
-        }
-    };
-    auto drain = [&](uint32_t bar, unsigned parity) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < kTmaWaitNs) {}
-    };
+    // bounded in time (kTmaWaitNs), or as soon as another thread of the block gave up
+    auto wait = [&](uint32_t bar, unsigned parity) { return bounded_wait(bar, parity, abort_flag, p.status, kTmaWaitNs); };
+    auto drain = [&](uint32_t bar, unsigned parity) { bounded_drain(bar, parity, kTmaWaitNs); };
     auto plane_of = [&](int k) { return wrapi(z0 - 1 + k, p.nz); };
 
     if (warp >= kLoader) {

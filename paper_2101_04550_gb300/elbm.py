@@ -36,7 +36,7 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
            "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
-           "elbm_step_noalloc"]
+           "elbm_step_noalloc", "elbm_selftest_wait_timeout"]
 
 
 class ElbmError(RuntimeError):
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
         L.elbm_get_u_ref.argtypes = [vp, ctypes.POINTER(dp)]
         L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
         L.elbm_batch_step.argtypes = [vp, ip]
+        L.elbm_selftest_wait_timeout.argtypes = [ip, vp]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
         L.elbm_batch_add.argtypes = [vp, vp]
         L.elbm_batch_remove.argtypes = [vp, vp]
@@ -317,3 +318,13 @@ def _addr(b):
     if isinstance(b, np.ndarray):
         return ctypes.c_void_p(b.ctypes.data)
     return b
+
+
+def selftest_wait_timeout(limit_ms=50, stream=None):
+    """Run the library's bounded device-side wait on a barrier that never
+    completes; returns the error code (ELBM_ERR_TIMEOUT, -6, when it gave up
+    as designed) and the library's message."""
+    L = load()
+    sp = None if stream is None else ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = L.elbm_selftest_wait_timeout(int(limit_ms), sp)
+    return rc, L.elbm_last_error().decode()

@@ -72,3 +72,9 @@ def test_null_handles(lib):
     assert lib.elbm_step(None, 1) == -1
     assert lib.elbm_sync(None) == -1
     assert lib.elbm_cells(None) == 0
+
+
+def test_selftest_rejects_a_bound_out_of_range(lib):
+    """The failure-detection self-test checks its bound before any CUDA call."""
+    for ms in (0, -5, 2001):
+        assert lib.elbm_selftest_wait_timeout(ms, None) == -1
