@@ -292,9 +292,9 @@ def main():
     Q = 27
     alg_bytes_per_cell = 2 * Q * s_bytes
 
-    def timed_run(storage, kernel, steps, reduce_every):
+    def timed_run(storage, kernel, steps, reduce_every, T=None):
         stream = torch.cuda.current_stream()
-        s = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"],
+        s = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"] if T is None else T,
                         nu=w["nu"], storage=storage, stream=stream, kernel=kernel)
         s.init(torch.as_tensor(rho, device="cuda"), torch.as_tensor(u, device="cuda"))
         s.step(args.warmup)
@@ -374,9 +374,13 @@ def main():
     # ---- variants (same workload, other storage / kernel form) ----------
     variants = {}
     if not args.no_variants and rank == 0:
-        for name, st, ker in (("f32_shift_two_pass", elbm.F32_SHIFT, 1), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2),
-                              ("f16_shift_single_pass", elbm.F16_SHIFT, 3), ("f16_shift_two_pass", elbm.F16_SHIFT, 1)):
-            sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every)
+        for name, st, ker, T in (("f32_shift_two_pass", elbm.F32_SHIFT, 1, None),
+                                 ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2, None),
+                                 ("f16_shift_single_pass", elbm.F16_SHIFT, 3, None),
+                                 ("f16_shift_two_pass", elbm.F16_SHIFT, 1, None),
+                                 ("f32_shift_single_pass_T0.5", elbm.F32_SHIFT, 3, 0.5),
+                                 ("f16_shift_single_pass_T0.5", elbm.F16_SHIFT, 3, 0.5)):
+            sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every, T)
             sv.close()
             nsteps = min(args.steps, 200)
             b = 2 * Q * elbm.STORAGE_BYTES[st]
