@@ -377,9 +377,7 @@ def main():
         for name, st, ker, T in (("f32_shift_two_pass", elbm.F32_SHIFT, 1, None),
                                  ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2, None),
                                  ("f16_shift_single_pass", elbm.F16_SHIFT, 3, None),
-                                 ("f16_shift_two_pass", elbm.F16_SHIFT, 1, None),
-                                 ("f32_shift_single_pass_T0.5", elbm.F32_SHIFT, 3, 0.5),
-                                 ("f16_shift_single_pass_T0.5", elbm.F16_SHIFT, 3, 0.5)):
+                                 ("f16_shift_two_pass", elbm.F16_SHIFT, 1, None)):
             sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every, T)
             sv.close()
             nsteps = min(args.steps, 200)
