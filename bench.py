@@ -395,9 +395,11 @@ def main():
         nch = (c["nx"], c["ny"], c["nz"])
         crho, cu = inputs.channel(nch, tuple(c["stretch"]), u_center=0.1, perturbation=0.05, seed=0)
         stream = torch.cuda.current_stream()
-        for name, st in (("channel_f32_shift", elbm.F32_SHIFT), ("channel_f32", elbm.F32)):
+        for name, st, ker in (("channel_f32_single_pass", elbm.F32, 3), ("channel_f32_two_pass", elbm.F32, 1),
+                              ("channel_f32_shift_single_pass", elbm.F32_SHIFT, 3),
+                              ("channel_f32_shift_two_pass", elbm.F32_SHIFT, 1)):
             sc = elbm.Solver(elbm.D3Q27, nch, stretch=c["stretch"], T=c["T"], nu=c["nu"], storage=st,
-                             stream=stream, walls_y=True, force=(c["g"], 0.0, 0.0))
+                             stream=stream, walls_y=True, force=(c["g"], 0.0, 0.0), kernel=ker)
             sc.init(torch.as_tensor(crho, device="cuda"), torch.as_tensor(cu, device="cuda"))
             sc.step(args.warmup)
             sc.sync()

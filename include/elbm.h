@@ -82,8 +82,9 @@ extern "C" {
  *       (TMA-fed, populations parked in tensor memory, when nx is a multiple
  *       of 32 and ny of 16; 32 x 8 TMA tiles when ny is a multiple of 8;
  *       cp.async-staged otherwise).  Setting it allocates the second array.
- *   The second-order equilibrium, walls and the body force always run in the
- *   two-pass form, whatever form is set. */
+ *   The second-order equilibrium always runs in the two-pass form; walls and
+ *   the body force run in form 3 only on its TMEM geometry (nx a multiple of
+ *   32, ny of 16) and in the two-pass form otherwise. */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3

@@ -160,11 +160,14 @@ void drop_graphs(elbm_solver* s)
 
 // Kernel form a step uses: 0 (automatic) means the two-pass form, which is
 // also the only form of the second-order equilibrium.
-// The second-order equilibrium, walls and the body force run in the two-pass form.
+// The second-order equilibrium runs in the two-pass form; walls and the body
+// force in the two-pass form or, where its geometry allows, the TMEM single pass.
 int effective_kernel(const elbm_solver* s)
 {
-    const bool special = s->eq_mode == 2 || s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
-    return (s->kernel != 0 && !special) ? s->kernel : 1;
+    if (s->kernel == 0 || s->eq_mode == 2) return 1;
+    const bool bounded = s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
+    if (!bounded) return s->kernel;
+    return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
 }
 
 size_t population_bytes(const elbm_solver* s)

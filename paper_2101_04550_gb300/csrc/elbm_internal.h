@@ -100,6 +100,7 @@ void fill_params(const Solver& s, StepParams& p);
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
+bool single_tmem_geometry(const Solver& s);
 template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);

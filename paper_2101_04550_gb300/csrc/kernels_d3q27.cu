@@ -16,4 +16,9 @@ template cudaError_t get_populations_impl<3>(const Solver&, void*, int, long lon
 template cudaError_t set_populations_impl<3>(const Solver&, const void*, int, long long*);
 template cudaError_t reduce_impl<3>(const Solver&, long long*);
 template cudaError_t field_sums_impl<3>(const Solver&, const void*, const void*, int, long long*);
+// Geometry the TMEM single pass takes (the arrays' 16-byte alignment aside).
+bool single_tmem_geometry(const Solver& s)
+{
+    return s.D == 3 && s.nx % kTileX == 0 && s.ny % kTmTileY == 0 && (s.nx * (int)storage_bytes(s.storage)) % 16 == 0;
+}
 }  // namespace elbm

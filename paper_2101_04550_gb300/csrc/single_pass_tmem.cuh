@@ -66,7 +66,10 @@ struct TmemLayout {
     static_assert(tile_bytes % 128 == 0, "tile boxes must keep 128-byte alignment");
 };
 
-template <int ST>
+// BC: walls (half-way bounce-back below y = 0 and above y = ny-1, with the
+// anomaly's negated ghost value in the central difference) and the body force,
+// read from the parameter block as in the two-pass kernels.
+template <int ST, bool BC = false>
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_single_pass_tmem(const __grid_constant__ CUtensorMap tm_tile, const __grid_constant__ CUtensorMap tm_row,
                        const __grid_constant__ CUtensorMap tm_out, StepParams p, void* dst)
@@ -284,7 +287,10 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             float d[3] = {0.f, 0.f, 0.f};
             if (p.eq_mode == 0) {
                 d[0] = (QX(sc, ty, tx + 2) - QX(sc, ty, tx)) * p.inv_2lam[0];
-                d[1] = (QY(sc, ty + 2, tx) - QY(sc, ty, tx)) * p.inv_2lam[1];
+                float qyp = QY(sc, ty + 2, tx), qym = QY(sc, ty, tx);
+                if (BC && p.walls_y && gy == p.ny - 1) qyp = -QY(sc, ty + 1, tx);  // ghost beyond the wall
+                if (BC && p.walls_y && gy == 0) qym = -QY(sc, ty + 1, tx);
+                d[1] = (qyp - qym) * p.inv_2lam[1];
                 d[2] = (qz_next - qz_prev) * p.inv_2lam[2];
             }
             const int z = z0 + k - 2;
@@ -296,12 +302,17 @@ __global__ void __launch_bounds__(kTmThreads, 1)
                 const float v = S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn);
                 if (cx_of(i) == 0 && ((tma_mask >> ((cy_of(i) + 1) + 3 * (cz_of<3>(i) + 1))) & 1u)) {
                     stage[((cy_of(i) + 1) + 3 * (cz_of<3>(i) + 1)) * kTmTileY * kTileX] = S::cvt(v);
+                } else if (BC && p.walls_y && ((cy_of(i) == 1 && gy == p.ny - 1) || (cy_of(i) == -1 && gy == 0))) {
+                    // half-way bounce-back: f'_i returns reversed to its own node, as
+                    // population opp(i), stored against opp(i)'s baseline
+                    const float vb = S::shifted ? v + bounce_rebase<3>(p, 26 - i) : v;
+                    S::store(out + opaque((26 - i) * p.N) + gx + gy * p.nx + z * p.plane, vb);
                 } else {
                     const int slot = opaque(i * p.N) + (xo[cx_of(i) + 1] + yz[(cy_of(i) + 1) + 3 * (cz_of<3>(i) + 1)]);
                     S::store(out + slot, v);
                 }
             };
-            relax_streamed<3>(p, gval, put, drho, j, d);
+            relax_streamed<3, false, BC>(p, gval, put, drho, j, d);
             fence_proxy_async_smem();
             mbar_arrive(out_ready(kc & 1));
             qz_prev = qz_cur;
@@ -329,7 +340,7 @@ bool single_tmem_ok(const Solver& s, const void* src, const void* dst)
            ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
 }
 
-template <int ST>
+template <int ST, bool BC = false>
 cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, bool* launched)
 {
     *launched = false;
@@ -338,11 +349,11 @@ cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, 
     if (encode_population_maps(s, p.f, kTmTileY, &tm_tile, &tm_row) != cudaSuccess) return cudaSuccess;
     if (encode_store_map(s, dst, kTileX, kTmTileY, &tm_out) != cudaSuccess) return cudaSuccess;
     const int smem = TmemLayout<ST>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_single_pass_tmem<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_single_pass_tmem<ST, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(s.nx / kTileX), (unsigned)(s.ny / kTmTileY),
                     (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
-    k_single_pass_tmem<ST><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, tm_out, p, dst);
+    k_single_pass_tmem<ST, BC><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, tm_out, p, dst);
     *launched = true;
     return cudaGetLastError();
 }
@@ -368,6 +379,13 @@ cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
         cudaError_t e = cudaSuccess;
         ELBM_DISPATCH_STORAGE(s.storage, {
             bool done = false;
+            if (p.walls_y || p.forced) {
+                // walls and body force: the TMEM form only (the caller checks its geometry)
+                e = launch_single_tmem<ST, true>(s, p, dst, &done);
+                if (e == cudaSuccess && !done) e = cudaErrorNotSupported;
+                if (e == cudaSuccess) ++*launches;
+                return e;
+            }
             e = launch_single_tmem<ST>(s, p, dst, &done);
             if (e == cudaSuccess && !done) e = launch_single_tma<ST>(s, p, dst, &done);
             if (e != cudaSuccess || done) {

@@ -147,8 +147,8 @@ def test_wall_gradient_reduction():
 
 
 def test_requested_kernel_forms_fall_back_bitwise():
-    """Walls and force run in the two-pass form whatever form is requested;
-    the results are bit-identical."""
+    """On a grid the TMEM single pass does not take (nx = 24), walls and force
+    run in the two-pass form whatever form is requested; bit-identical."""
     rho, u = inputs.channel(CHANNEL_N, CHANNEL_LAM, u_center=0.05, perturbation=0.05, seed=1)
     out = []
     for kernel in (1, 2, 3):
@@ -173,3 +173,35 @@ def test_batch_rejects_walls_and_force():
             elbm.Batch([a, bad])
     for s in (a, b, c):
         s.close()
+
+
+TMEM_N = (64, 32, 20)
+
+
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT, elbm.F16_SHIFT])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_single_pass_walls_and_force_bitwise(storage, steps):
+    """The TMEM single pass with walls and body force (nx a multiple of 32,
+    ny of 16) against the two-pass form: bit-identical populations, rest
+    storage baseline, both parities."""
+    rho, u = inputs.channel(TMEM_N, CHANNEL_LAM, u_center=0.05, perturbation=0.05, seed=3)
+    out = []
+    for kernel in (1, 3):
+        with elbm.Solver(elbm.D3Q27, TMEM_N, stretch=CHANNEL_LAM, T=CHANNEL_T, nu=0.02, storage=storage,
+                         kernel=kernel, walls_y=True, force=(2e-5, 0, 0)) as s:
+            s.init(rho, u)
+            s.step(steps)
+            out.append(s.get_populations())
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("storage,u_ref", [(elbm.F32_SHIFT, None), (elbm.F16_SHIFT, (0.0333, 0.0, 0.0))])
+def test_single_pass_channel_against_oracle(storage, u_ref):
+    """The TMEM single pass with walls and force against the oracle after 201
+    steps; with FP16 storage at a moving baseline (bounced populations are
+    rebased when they are written, where the two-pass form rebases them when
+    read, so the two forms differ by FP16 rounding there)."""
+    rho, u = inputs.channel(TMEM_N, CHANNEL_LAM, u_center=0.05, perturbation=0.05, seed=0)
+    (_, ug), (_, uo) = run_pair(elbm.D3Q27, TMEM_N, CHANNEL_LAM, CHANNEL_T, 0.02, rho, u, 201, storage,
+                                force=(2e-5, 0.0, 0.0), kernel=3, u_ref=u_ref)
+    assert rel_linf(ug, uo) <= TOL[storage]
