@@ -52,7 +52,8 @@ MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47
                     # 218.5 B/node measured at 192^3 (profiles/k_single_pass_tmem_d3q27_hit192_f32.md) x 256^3
                     ("ea6c7fce23e1af60", "f32s", 3): 3.666e9,
                     # 217.3 B/node measured at 192^3 with the TMA-store form, x 256^3
-                    ("8b7c40bddffd89cf", "f32s", 3): 3.646e9}
+                    ("8b7c40bddffd89cf", "f32s", 3): 3.646e9,
+                    ("93127f9738070902", "f32s", 3): 3.647e9}
 
 
 def kernel_source_hash() -> str:
