@@ -179,6 +179,20 @@ int elbm_set_populations(elbm_solver* s, const void* f, int dtype, int on_device
  * Returns ELBM_ERR_NONFINITE (after filling out) if a node is non-finite. */
 int elbm_reduce(elbm_solver* s, double* out);
 
+/*
+ * FP64 projection of the velocity on one Fourier mode, the amplitude
+ * measurement of the shear-wave viscosity test (Sec. III.A):
+ *   out[0] = sum_x (u(x) . dir) cos(k . x),  out[1] = sum_x (u(x) . dir) sin(k . x)
+ * over every node, with x = (i lam_x, j lam_y, k lam_z) the node's physical
+ * position, u the reported velocity (as elbm_moments gives it), k[3] the
+ * wavevector in physical units and dir[3] the projection direction (the
+ * z components are ignored for D2Q9).  The mode's amplitude is
+ * 2 sqrt(out[0]^2 + out[1]^2) / N.  Synchronises the solver's stream.
+ * Errors: ELBM_ERR_ARG (NULL or non-finite arguments), ELBM_ERR_STATE
+ * (before init), ELBM_ERR_CUDA.
+ */
+int elbm_mode_sums(elbm_solver* s, const double* k, const double* dir, double* out);
+
 /* Block the host until the solver's stream is idle. */
 int elbm_sync(elbm_solver* s);
 

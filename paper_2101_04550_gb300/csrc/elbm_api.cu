@@ -557,6 +557,26 @@ int elbm_reduce(elbm_solver* s, double* out)
     return ELBM_OK;
 }
 
+int elbm_mode_sums(elbm_solver* s, const double* k, const double* dir, double* out)
+{
+    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
+    if (!s || !k || !dir || !out) return fail(ELBM_ERR_ARG, "NULL argument");
+    if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_mode_sums before init");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(k[a]) || !std::isfinite(dir[a])) return fail(ELBM_ERR_ARG, "k and dir must be finite");
+    cudaError_t e = ensure_reduce_scratch(s);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_mode_sums scratch");
+    e = (s->D == 2) ? elbm::mode_sums_impl<2>(*s, k, dir, &s->launches)
+                    : elbm::mode_sums_impl<3>(*s, k, dir, &s->launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->host_red, s->red_out, sizeof(double) * ELBM_NRED, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "elbm_mode_sums");
+    out[0] = s->host_red[0];
+    out[1] = s->host_red[1];
+    return check_status(s);
+}
+
 long long elbm_cells(const elbm_solver* s) { return s ? s->N : 0; }
 long long elbm_steps_done(const elbm_solver* s) { return s ? s->steps_done : 0; }
 double elbm_omega(const elbm_solver* s) { return s ? s->omega : 0.0; }

@@ -107,6 +107,7 @@ template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long
 template <int D> cudaError_t get_populations_impl(const Solver&, void*, int, long long*);
 template <int D> cudaError_t set_populations_impl(const Solver&, const void*, int, long long*);
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
+template <int D> cudaError_t mode_sums_impl(const Solver&, const double*, const double*, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t batch_enqueue_impl(int, int, int, int, cudaStream_t, long long*);
 template <int D> cudaError_t batch_upload_impl(int, const BatchMember*, int, cudaStream_t);

@@ -15,5 +15,6 @@ template cudaError_t moments_impl<2>(const Solver&, void*, void*, int, long long
 template cudaError_t get_populations_impl<2>(const Solver&, void*, int, long long*);
 template cudaError_t set_populations_impl<2>(const Solver&, const void*, int, long long*);
 template cudaError_t reduce_impl<2>(const Solver&, long long*);
+template cudaError_t mode_sums_impl<2>(const Solver&, const double*, const double*, long long*);
 template cudaError_t field_sums_impl<2>(const Solver&, const void*, const void*, int, long long*);
 }  // namespace elbm

@@ -15,6 +15,7 @@ template cudaError_t moments_impl<3>(const Solver&, void*, void*, int, long long
 template cudaError_t get_populations_impl<3>(const Solver&, void*, int, long long*);
 template cudaError_t set_populations_impl<3>(const Solver&, const void*, int, long long*);
 template cudaError_t reduce_impl<3>(const Solver&, long long*);
+template cudaError_t mode_sums_impl<3>(const Solver&, const double*, const double*, long long*);
 template cudaError_t field_sums_impl<3>(const Solver&, const void*, const void*, int, long long*);
 // Geometry the TMEM single pass takes (the arrays' 16-byte alignment aside).
 bool single_tmem_geometry(const Solver& s)

@@ -540,6 +540,62 @@ cudaError_t field_sums_impl(const Solver& s, const void* rho, const void* u, int
     return cudaGetLastError();
 }
 
+// Shear-mode projection (the amplitude of the shear wave, Sec. III.A):
+// out[0] = sum_x (u . dir) cos(k . x), out[1] = sum_x (u . dir) sin(k . x), in
+// FP64, with x = (i lam_x, j lam_y, k lam_z) the node's physical position and
+// u the reported velocity.  The phase is reduced modulo 2 pi in FP64.
+struct ModeArgs {
+    double k[3], dir[3];
+};
+
+template <int D, int ST>
+__global__ void __launch_bounds__(kBlock) k_mode_sums(StepParams p, ModeArgs m, double* partials)
+{
+    double acc[ELBM_NRED];
+#pragma unroll
+    for (int q = 0; q < ELBM_NRED; ++q) acc[q] = 0.0;
+    acc[9] = DBL_MAX;
+    for (int cell = blockIdx.x * kBlock + threadIdx.x; cell < p.N; cell += gridDim.x * kBlock) {
+        const Node n = make_node<D>(p, cell);
+        float g[Lat<D>::Q];
+        gather_any<D, ST>(p, n, g);
+        float drho, j[3];
+        moments<D>(p, g, drho, j);
+        const float inv_r = 1.0f / (p.rho_ref + drho);
+        double us = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) us += (double)(j[a] * inv_r + 0.5f * p.g[a]) * m.dir[a];
+        const int z = (D == 3) ? cell / p.plane : 0;
+        const int r = cell - z * p.plane;
+        const int y = r / p.nx, x = r - y * p.nx;
+        const double phase = m.k[0] * x * (double)p.lam[0] + m.k[1] * y * (double)p.lam[1] +
+                             (D == 3 ? m.k[2] * z * (double)p.lam[2] : 0.0);
+        double sn, cs;
+        sincos(phase, &sn, &cs);
+        acc[0] += us * cs;
+        acc[1] += us * sn;
+    }
+    block_reduce(acc, partials + (size_t)blockIdx.x * ELBM_NRED);
+}
+
+template <int D>
+cudaError_t mode_sums_impl(const Solver& s, const double* k, const double* dir, long long* launches)
+{
+    StepParams p;
+    fill_params(s, p);
+    ModeArgs m;
+    for (int a = 0; a < 3; ++a) {
+        m.k[a] = k[a];
+        m.dir[a] = dir[a];
+    }
+    ELBM_DISPATCH_STORAGE(s.storage, {
+        k_mode_sums<D, ST><<<s.red_blocks, kBlock, 0, s.stream>>>(p, m, s.partials);
+    });
+    k_red_final<D><<<1, kBlock, 0, s.stream>>>(s.partials, s.red_blocks, s.red_out);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
 template <int D>
 cudaError_t reduce_impl(const Solver& s, long long* launches)
 {

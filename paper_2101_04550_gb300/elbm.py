@@ -36,7 +36,7 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
            "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
-           "elbm_step_noalloc", "elbm_selftest_wait_timeout"]
+           "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums"]
 
 
 class ElbmError(RuntimeError):
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
         L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
         L.elbm_batch_step.argtypes = [vp, ip]
         L.elbm_selftest_wait_timeout.argtypes = [ip, vp]
+        L.elbm_mode_sums.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
         L.elbm_batch_add.argtypes = [vp, vp]
         L.elbm_batch_remove.argtypes = [vp, vp]
@@ -227,6 +228,15 @@ class Solver:
     def set_populations(self, f):
         b, on, code = _buffer(f, np.float64)
         _check(load().elbm_set_populations(self._h, _addr(b), code, on))
+
+    def mode_amplitude(self, k, direction):
+        """Amplitude 2 |sum_x (u . s) exp(-i k . x)| / N of one Fourier mode of
+        the velocity, accumulated in FP64 on the GPU (k in physical units)."""
+        kk = (ctypes.c_double * 3)(*[float(v) for v in (list(k) + [0.0] * 3)[:3]])
+        dd = (ctypes.c_double * 3)(*[float(v) for v in (list(direction) + [0.0] * 3)[:3]])
+        out = (ctypes.c_double * 2)()
+        _check(load().elbm_mode_sums(self._h, kk, dd, out))
+        return 2.0 * float(np.hypot(out[0], out[1])) / self.N
 
     def reduce(self, raise_nonfinite=True):
         out = (ctypes.c_double * NRED)()

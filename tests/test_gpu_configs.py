@@ -29,8 +29,9 @@ def _gpu():
 
 
 def gpu_nu(n, lam, k_dir, s_dir, U, T, nu, steps=1000, every=50, t_min=100):
-    """Viscosity from the decay of the shear mode's Fourier amplitude, run on
-    the GPU (reading c8: least squares on ln A after step t_min)."""
+    """Viscosity from the decay of the shear mode's Fourier amplitude, both
+    measured on the GPU (FP64 mode projection, elbm_mode_sums), fitted on the
+    host (reading c8: least squares on ln A after step t_min)."""
     D = len(n)
     rho, u, k, s = inputs.shear_wave(n, lam, k_dir, s_dir, 1e-3, U)
     ts, A = [], []
@@ -41,8 +42,23 @@ def gpu_nu(n, lam, k_dir, s_dir, U, T, nu, steps=1000, every=50, t_min=100):
             if t:
                 s_.step(every)
             ts.append(t)
-            A.append(mode_amplitude(s_.moments()[1].astype(np.float64), k, s, lam))
+            A.append(s_.mode_amplitude(k, s))
     return decay_rate(ts, A, t_min) / (k @ k)
+
+
+@pytest.mark.parametrize("lattice,n,lam,kd,sd", [(elbm.D2Q9, (64, 128), (2.0, 1.0), (1, 1), (-1, 1)),
+                                                  (elbm.D3Q27, (32, 16, 24), (1.0, 1.5, 2.0), (1, 0, 1), (-1, 0, 1))])
+def test_mode_projection_on_gpu_matches_numpy(lattice, n, lam, kd, sd):
+    """elbm_mode_sums (FP64 on the GPU) against the numpy projection of the
+    velocity read back from the GPU, on a stretched lattice."""
+    rho, u, k, s = inputs.shear_wave(n, lam, kd, sd, 1e-2, 0.1)
+    with elbm.Solver(lattice, n, stretch=lam, T=0.4, nu=0.02, storage=elbm.F32_SHIFT) as sv:
+        sv.init(rho, u)
+        sv.step(37)
+        got = sv.mode_amplitude(k, s)
+        _, ug = sv.moments()
+    want = mode_amplitude(ug.astype(np.float64), k, s, lam)
+    assert abs(got - want) <= 1e-9 * want + 1e-15
 
 
 def test_shear_wave_viscosity_on_gpu():
