@@ -181,21 +181,6 @@ __device__ __forceinline__ void tmem_load27(uint32_t t, float* v)
     for (int i = 0; i < 27; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Bulk tensor store of a box from shared memory (the bulk-group completion
-// mechanism: commit, then wait until the source may be reused / the writes are done).
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3, uint32_t src)
-{
-    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// Order this thread's shared-memory writes before later reads by the async (TMA) proxy.
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // Shared-memory layout (byte offsets from a 128-byte aligned base).  TMA
 // destinations start on 128-byte boundaries.
 template <int ST>
@@ -403,9 +388,6 @@ bool single_tma_ok(const Solver& s, const void* src, const void* dst)
 // Tensor maps of one population array: dims (x, y, z, population), boxes of
 // the tile (32 x tile_y x 1 x 27) and of one ring row (32 x 1 x 1 x 27).
 cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row);
-// Tensor map of one population array for stores: boxes of box_x x box_y x 1 x 1
-// (one population of one plane).
-cudaError_t encode_store_map(const Solver& s, const void* f, int box_x, int box_y, CUtensorMap* map);
 
 template <int ST>
 cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, bool* launched)

@@ -5,15 +5,13 @@
 // A block of five warpgroups owns a tile of 32 x 16 columns and marches
 // through kSegPlanes z planes:
 //   * the first warp of warpgroup 4 loads plane k of the tile with one 4-D
-//     TMA box (x 32, y 16, z 1, population 27) into a ring of two
-//     shared-memory buffers, and the ring of nodes around the tile -- two TMA
-//     row boxes and two columns of 16 nodes by cp.async -- into a ring of two
-//     buffers; one mbarrier per buffer ("full") tracks both kinds of copy;
-//   * one lane of its second warp writes the nine populations with cx = 0 of
-//     every relaxed plane with bulk tensor stores (their target rows are the
-//     tile's own, 16-byte aligned x range) from a two-deep staging ring; the
-//     other 18 populations, shifted by one node in x, are written with plain
-//     coalesced stores by the consumers;
+//     TMA box (x 32, y 16, z 1, population 27) into a ring of tile buffers in
+//     shared memory, and the ring of nodes around the tile -- two TMA row
+//     boxes and two columns of 16 nodes by cp.async -- into a ring of two
+//     buffers; one mbarrier per buffer ("full") tracks both kinds of copy.
+//     The other warps of warpgroup 4 only fill it up: TMEM lane quarters
+//     follow a warp's rank within its warpgroup, so the consumers must make
+//     whole warpgroups;
 //   * the 16 warps of warpgroups 0..3 each own one tile row.  For plane k a
 //     thread reads its node's 27 populations from shared memory once, hands
 //     the buffer back ("empty" mbarrier), parks the values in its TMEM lane,
@@ -21,15 +19,18 @@
 //     rotates over the warps from plane to plane), publishes them ("qready")
 //     and relaxes plane k-1 -- with the values parked one plane earlier --
 //     once every warp has published the anomaly of plane k-1 (the central
-//     difference of Eq. Paastar1 needs the face neighbours).
-// Because a tile buffer comes back as soon as it has been read, two buffers
-// let the loads run two planes ahead of the anomaly pass.  Moving a third of
-// the output through the TMA store path raised the step rate by about 13 %:
-// the plain-store path of an SM was the limit.  There is no block-wide barrier
-// in the loop.  Every wait is bounded (2 s, or as soon as another thread of
-// the block gave up); a wait that gives up sets ELBM_ERR_TIMEOUT in the status
-// word, and the block winds down: the loader waits, again bounded, for the
-// copies in flight, and the TMEM is freed by the warp that allocated it.
+//     difference of Eq. Paastar1 needs the face neighbours), pushing the 27
+//     results with coalesced stores.
+// Shared memory is kept small on purpose: an SM's shared memory and its L1
+// cache are carved from one array, and the step rate grew as the footprint
+// shrank.  A tile buffer comes back as soon as it has been read, and the
+// relaxation of the previous plane covers the next load, so FP32 storage runs
+// fastest with a single buffer; 16-bit storage (half the bytes, more
+// arithmetic per byte) with two.  There is no block-wide barrier in the loop.
+// Every wait is bounded (2 s, or as soon as another thread of the block gave
+// up); a wait that gives up sets ELBM_ERR_TIMEOUT in the status word, and the
+// block winds down: the loader waits, again bounded, for the copies in flight,
+// and the TMEM is freed by the warp that allocated it.
 #pragma once
 #include "single_pass_tma.cuh"
 
@@ -44,6 +45,7 @@ template <int ST>
 struct TmemLayout {
     using T = typename Storage<ST>::T;
     static constexpr int es = (int)sizeof(T);
+    static constexpr int ntile = es == 4 ? 1 : 2;                    // tile buffers
     static constexpr int tile_bytes = 27 * kTmTileY * kTileX * es;   // one plane of the tile
     static constexpr int row_box_bytes = 27 * kTileX * es;           // one ring row, all populations
     static constexpr int row_stride = (row_box_bytes + 127) / 128 * 128;
@@ -51,15 +53,13 @@ struct TmemLayout {
     static constexpr int cols_bytes = 27 * ncol * 4;                 // as 4-byte words
     static constexpr int qx_bytes = kTmTileY * (kTileX + 2) * 4;
     static constexpr int qy_bytes = (kTmTileY + 2) * kTileX * 4;
-    static constexpr int off_tile = 0;                               // [2] planes
-    static constexpr int off_rows = off_tile + 2 * tile_bytes;       // [2 slots][2 sides]
+    static constexpr int off_tile = 0;                               // [ntile] planes
+    static constexpr int off_rows = off_tile + ntile * tile_bytes;   // [2 slots][2 sides]
     static constexpr int off_cols = off_rows + 4 * row_stride;       // [2 slots]
-    static constexpr int stage_bytes = 9 * kTmTileY * kTileX * es;   // outputs of the 9 populations with cx = 0
-    static constexpr int off_stage = (off_cols + 2 * cols_bytes + 127) / 128 * 128;  // [2 slots]
-    static constexpr int off_qx = off_stage + 2 * stage_bytes;         // [kTmaQSlots]
+    static constexpr int off_qx = off_cols + 2 * cols_bytes;         // [kTmaQSlots]
     static constexpr int off_qy = off_qx + kTmaQSlots * qx_bytes;
     static constexpr int off_bar = (off_qy + kTmaQSlots * qy_bytes + 7) / 8 * 8;
-    static constexpr int nbar = 14 + kTmaQSlots;
+    static constexpr int nbar = 8 + kTmaQSlots;
     static constexpr int off_abort = off_bar + 8 * nbar;
     static constexpr int off_tmem = off_abort + 4;
     static constexpr int bytes = off_abort + 16 + 128;               // + slack for aligning the base
@@ -72,7 +72,7 @@ struct TmemLayout {
 template <int ST, bool BC = false>
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_single_pass_tmem(const __grid_constant__ CUtensorMap tm_tile, const __grid_constant__ CUtensorMap tm_row,
-                       const __grid_constant__ CUtensorMap tm_out, StepParams p, void* dst)
+                       StepParams p, void* dst)
 {
     using S = Storage<ST>;
     using T = typename S::T;
@@ -83,12 +83,10 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     unsigned char* base = smem_raw + (sbase - raw_addr);
     const uint32_t bar0 = sbase + L::off_bar;
     auto full_t = [&](int b) { return bar0 + 8u * b; };
-    auto empty_t = [&](int b) { return bar0 + 8u * (3 + b); };
-    auto full_r = [&](int r) { return bar0 + 8u * (6 + r); };
-    auto empty_r = [&](int r) { return bar0 + 8u * (8 + r); };
-    auto qready = [&](int s) { return bar0 + 8u * (10 + s); };
-    auto out_ready = [&](int s) { return bar0 + 8u * (10 + kTmaQSlots + s); };
-    auto out_free = [&](int s) { return bar0 + 8u * (12 + kTmaQSlots + s); };
+    auto empty_t = [&](int b) { return bar0 + 8u * (2 + b); };
+    auto full_r = [&](int r) { return bar0 + 8u * (4 + r); };
+    auto empty_r = [&](int r) { return bar0 + 8u * (6 + r); };
+    auto qready = [&](int s) { return bar0 + 8u * (8 + s); };
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L::off_abort);
 
     const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTmTileY;
@@ -97,15 +95,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kLoader = kTmConsumers / 32;  // first warp of the loading warpgroup
-    // The 9 populations with cx = 0 land on 16-byte aligned rows (the tile's
-    // own x range) and leave through TMA stores, bit (cy+1) + 3 (cz+1); those
-    // whose rows would wrap in y (edge tiles) take plain stores like the rest.
-    unsigned tma_mask = 0x1ffu;
-    if (y0 == 0) tma_mask &= ~0x49u;                 // cy = -1
-    if (y0 + kTmTileY == p.ny) tma_mask &= ~0x124u;  // cy = +1
 
     if (threadIdx.x == 0) {
-        for (int b = 0; b < 3; ++b) {
+        for (int b = 0; b < L::ntile; ++b) {
             mbar_init(full_t(b), 1);
             mbar_init(empty_t(b), kTmConsumers);
         }
@@ -114,10 +106,6 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             mbar_init(empty_r(r), kTmConsumers);
         }
         for (int s = 0; s < kTmaQSlots; ++s) mbar_init(qready(s), kTmConsumers);
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(out_ready(s), kTmConsumers);
-            mbar_init(out_free(s), 1);
-        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -143,9 +131,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             const int cxl = wrapi(x0 - 1, p.nx), cxr = wrapi(x0 + kTileX, p.nx);
             int issued = 0;
             for (int k = 0; k < K; ++k) {
-                const int b = k % 2, r = k & 1;
+                const int b = k % L::ntile, r = k & 1;
                 bool ok = true;
-                if (k >= 2) ok = wait(empty_t(b), ((k / 2) - 1) & 1);
+                if (k >= L::ntile) ok = wait(empty_t(b), ((k / L::ntile) - 1) & 1);
                 if (ok && k >= 2) ok = wait(empty_r(r), ((k / 2) - 1) & 1);
                 if (!__all_sync(0xffffffffu, ok)) break;
                 const int zk = plane_of(k);
@@ -170,29 +158,10 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             cp_async_wait_all();
             // no copy may still be in flight when the block retires
             if (lane == 0) {
-                for (int k = max(0, issued - 2); k < issued; ++k) drain(full_t(k % 2), (k / 2) & 1);
+                for (int k = max(0, issued - L::ntile); k < issued; ++k) drain(full_t(k % L::ntile), (k / L::ntile) & 1);
                 for (int k = max(0, issued - 2); k < issued; ++k) drain(full_r(k & 1), (k / 2) & 1);
             }
             __syncwarp();
-        } else if (warp == kLoader + 1 && lane == 0) {
-            // ---------------------------------------------- output stores
-            // every plane: once all consumers have staged it, one bulk tensor
-            // store per population with cx = 0 (box 32 x 16 at (x0, y0 + cy, z + cz))
-            for (int kc = 1; kc <= K - 2; ++kc) {
-                const int so = kc & 1;
-                if (!wait(out_ready(so), ((kc - 1) / 2) & 1)) break;
-                const int z = z0 + kc - 1;
-                for (int jj = 0; jj < 9; ++jj) {
-                    if (!((tma_mask >> jj) & 1u)) continue;
-                    const int cy = jj % 3 - 1, cz = jj / 3 - 1, i = 1 + 3 * (cy + 1) + 9 * (cz + 1);
-                    const uint32_t src = sbase + L::off_stage + so * L::stage_bytes + jj * (L::stage_bytes / 9);
-                    tma_store_4d(&tm_out, x0, y0 + cy, wrapi(z + cz, p.nz), i, src);
-                }
-                bulk_commit();
-                bulk_wait_read();  // the staging slot may be refilled once the stores have read it
-                mbar_arrive(out_free(so));
-            }
-            bulk_wait_all();
         }
     } else {
         // ------------------------------------------------------ consumers
@@ -225,8 +194,8 @@ __global__ void __launch_bounds__(kTmThreads, 1)
         // moments of the own node of the plane relaxed next (computed with its anomaly)
         float m_drho = 0.f, m_j[3] = {0.f, 0.f, 0.f};
         for (int k = 0; k < K; ++k) {
-            const int b = k % 2, r = k & 1, s = k % kTmaQSlots;
-            const bool got = wait(full_t(b), (k / 2) & 1) && wait(full_r(r), (k / 2) & 1);
+            const int b = k % L::ntile, r = k & 1, s = k % kTmaQSlots;
+            const bool got = wait(full_t(b), (k / L::ntile) & 1) && wait(full_r(r), (k / 2) & 1);
             if (!__all_sync(0xffffffffu, got)) break;
             float q[3], k_drho, k_j[3];
             {
@@ -277,8 +246,6 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             const float qz_next = q[2];
             const int kc = k - 1, sc = kc % kTmaQSlots;
             if (!__all_sync(0xffffffffu, wait(qready(sc), (kc / kTmaQSlots) & 1))) break;
-            if (kc >= 3 && !__all_sync(0xffffffffu, wait(out_free(kc & 1), ((kc - 3) / 2) & 1))) break;
-            T* stage = reinterpret_cast<T*>(base + L::off_stage + (kc & 1) * L::stage_bytes) + ty * kTileX + tx;
             float g[27];
             tmem_wait_st();
             tmem_load27(t_own + (uint32_t)((kc & 1) * 128), g);
@@ -300,9 +267,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             for (int c = 0; c < 9; ++c) yz[c] = yo[c % 3] + zo[c / 3];
             auto put = [&](int i, float gn) {
                 const float v = S::shifted ? gn : fmaf(p.bw[i], p.rho_ref, gn);
-                if (cx_of(i) == 0 && ((tma_mask >> ((cy_of(i) + 1) + 3 * (cz_of<3>(i) + 1))) & 1u)) {
-                    stage[((cy_of(i) + 1) + 3 * (cz_of<3>(i) + 1)) * kTmTileY * kTileX] = S::cvt(v);
-                } else if (BC && p.walls_y && ((cy_of(i) == 1 && gy == p.ny - 1) || (cy_of(i) == -1 && gy == 0))) {
+                if (BC && p.walls_y && ((cy_of(i) == 1 && gy == p.ny - 1) || (cy_of(i) == -1 && gy == 0))) {
                     // half-way bounce-back: f'_i returns reversed to its own node, as
                     // population opp(i), stored against opp(i)'s baseline
                     const float vb = S::shifted ? v + bounce_rebase<3>(p, 26 - i) : v;
@@ -313,8 +278,6 @@ __global__ void __launch_bounds__(kTmThreads, 1)
                 }
             };
             relax_streamed<3, false, BC>(p, gval, put, drho, j, d);
-            fence_proxy_async_smem();
-            mbar_arrive(out_ready(kc & 1));
             qz_prev = qz_cur;
             qz_cur = qz_next;
             m_drho = k_drho;
@@ -345,15 +308,14 @@ cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, 
 {
     *launched = false;
     if (!single_tmem_ok<ST>(s, p.f, dst)) return cudaSuccess;
-    CUtensorMap tm_tile, tm_row, tm_out;
+    CUtensorMap tm_tile, tm_row;
     if (encode_population_maps(s, p.f, kTmTileY, &tm_tile, &tm_row) != cudaSuccess) return cudaSuccess;
-    if (encode_store_map(s, dst, kTileX, kTmTileY, &tm_out) != cudaSuccess) return cudaSuccess;
     const int smem = TmemLayout<ST>::bytes;
     cudaError_t e = cudaFuncSetAttribute(k_single_pass_tmem<ST, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(s.nx / kTileX), (unsigned)(s.ny / kTmTileY),
                     (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
-    k_single_pass_tmem<ST, BC><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, tm_out, p, dst);
+    k_single_pass_tmem<ST, BC><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, p, dst);
     *launched = true;
     return cudaGetLastError();
 }

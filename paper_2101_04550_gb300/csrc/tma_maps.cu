@@ -51,19 +51,4 @@ cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, C
     return cudaSuccess;
 }
 
-cudaError_t encode_store_map(const Solver& s, const void* f, int box_x, int box_y, CUtensorMap* map)
-{
-    const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn || s.D != 3) return cudaErrorNotSupported;
-    const cuuint64_t es = storage_bytes(s.storage);
-    const cuuint64_t dims[4] = {(cuuint64_t)s.nx, (cuuint64_t)s.ny, (cuuint64_t)s.nz, 27};
-    const cuuint64_t strides[3] = {s.nx * es, (cuuint64_t)s.nx * s.ny * es, (cuuint64_t)s.N * es};
-    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, 1}, unit[4] = {1, 1, 1, 1};
-    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    const CUresult r = fn(map, dt, 4, const_cast<void*>(f), dims, strides, box, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 }  // namespace elbm
