@@ -207,16 +207,25 @@ long long elbm_launch_count(const elbm_solver* s);
 
 /* ------------------------------------------------------------- batches */
 /*
- * A batch advances many grids together: members share lattice, storage mode
- * and stream, and may differ in size, stretch, T and nu.  One batched step is
- * two launches (anomaly pass and collide pass of the two-pass form, Eqs. LBGK,
- * Deviation, Paastar1, 27eqext) over all members; every member's result is
- * bit-identical to stepping it alone.  The batch holds the solvers (it does
- * not own them) and a device table of their parameters, refreshed at every
- * elbm_batch_step; destroy the batch before any of its solvers.  A batch
- * holds at most 40 solvers, and one live batch per (lattice, storage mode)
- * and device may exist at a time (its member table lives in constant
- * memory); elbm_batch_create returns ELBM_ERR_STATE for a second one.
+ * A batch advances many grids together: members share lattice, storage mode,
+ * stream and kernel form, and may differ in size, stretch, T and nu; every
+ * member's result is bit-identical to stepping it alone.  The batch holds the
+ * solvers (it does not own them); destroy the batch before any of its solvers.
+ * A batch holds at most 40 solvers.  Its form follows its members' kernel
+ * form (ELBM_OPT_KERNEL and the grid decide it, as for elbm_step):
+ *  - two-pass members (periodic, unforced, extended or product-form
+ *    equilibrium): one batched step is two launches (anomaly pass and collide
+ *    pass of the two-pass form, Eqs. LBGK, Deviation, Paastar1, 27eqext) over
+ *    all members, from a table of their parameters in constant memory,
+ *    refreshed at every elbm_batch_step.  One live batch of this form per
+ *    (lattice, storage mode) and device may exist at a time;
+ *    elbm_batch_create returns ELBM_ERR_STATE for a second one;
+ *  - single-pass members (ELBM_OPT_KERNEL 3, D3Q27, two population arrays;
+ *    walls and body force allowed where the single pass takes them): each
+ *    member's sequence of nsteps single-pass steps is captured once as a CUDA
+ *    graph and replayed on private streams of the batch, so the members run
+ *    side by side.
+ * Mixing the forms in one batch returns ELBM_ERR_ARG.
  */
 typedef struct elbm_batch elbm_batch;
 
@@ -231,15 +240,18 @@ int elbm_batch_remove(elbm_batch* b, elbm_solver* s);
 int elbm_batch_size(const elbm_batch* b);
 
 /* Advance every member by nsteps >= 0 steps, asynchronously with respect to
- * the device, ordered after earlier work on the members' stream.  The first
- * batch of a (lattice, storage) kind in the process times one real step with
- * 128- and one with 256-thread blocks and keeps the faster for every later
- * batch of that kind (the autotuner); the launch sequence of nsteps steps is
- * captured once as a CUDA graph, on a stream of the batch's own, and replayed. */
+ * the device, ordered after earlier work on the members' stream.  Two-pass
+ * form: the first batch of a (lattice, storage) kind in the process times one
+ * real step with 128- and one with 256-thread blocks and keeps the faster for
+ * every later batch of that kind (the autotuner); the launch sequence of
+ * nsteps steps is captured once as a CUDA graph, on a stream of the batch's
+ * own, and replayed.  Single-pass form: see above; a member's graphs are
+ * released when it leaves (once their launches are complete). */
 int elbm_batch_step(elbm_batch* b, int nsteps);
 
-/* Chosen block size (0 before tuning), the two tuning step times in ms
- * (128, 256) and the number of kernel launches issued so far. */
+/* Chosen block size (0 before tuning, and for the single-pass form), the two
+ * tuning step times in ms (128, 256) and the number of kernel launches issued
+ * so far. */
 int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long long* launches);
 
 void elbm_batch_destroy(elbm_batch* b);

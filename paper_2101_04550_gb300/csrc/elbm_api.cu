@@ -1,6 +1,7 @@
 // C ABI of the elbm library (declared in include/elbm.h): argument checks,
 // ownership of device memory, choice of kernel form, host<->device staging.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -126,6 +127,18 @@ void fill_params(const Solver& s, StepParams& p)
     p.parity = s.parity;
 }
 
+// Kernel form a step uses: 0 (automatic) means the two-pass form, which is
+// also the only form of the second-order equilibrium.
+// The second-order equilibrium runs in the two-pass form; walls and the body
+// force in the two-pass form or, where its geometry allows, the TMEM single pass.
+int effective_kernel(const Solver* s)
+{
+    if (s->kernel == 0 || s->eq_mode == 2) return 1;
+    const bool bounded = s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
+    if (!bounded) return s->kernel;
+    return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
+}
+
 }  // namespace elbm
 
 using elbm::Solver;
@@ -156,18 +169,6 @@ void drop_graphs(elbm_solver* s)
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
-}
-
-// Kernel form a step uses: 0 (automatic) means the two-pass form, which is
-// also the only form of the second-order equilibrium.
-// The second-order equilibrium runs in the two-pass form; walls and the body
-// force in the two-pass form or, where its geometry allows, the TMEM single pass.
-int effective_kernel(const elbm_solver* s)
-{
-    if (s->kernel == 0 || s->eq_mode == 2) return 1;
-    const bool bounded = s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
-    if (!bounded) return s->kernel;
-    return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
 }
 
 size_t population_bytes(const elbm_solver* s)
@@ -223,7 +224,9 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
     if (storage != ELBM_F32 && storage != ELBM_F16_SHIFT && storage != ELBM_BF16_SHIFT && storage != ELBM_F32_SHIFT)
         return fail(ELBM_ERR_ARG, "unknown storage mode %d", storage);
 
+    static std::atomic<long long> next_uid{0};
     elbm_solver* s = new elbm_solver();
+    s->uid = ++next_uid;
     s->lattice = lattice;
     s->D = D;
     s->Q = lattice;
@@ -401,7 +404,7 @@ int elbm_step(elbm_solver* s, int n)
     if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
     if (n < 0) return fail(ELBM_ERR_ARG, "n must be >= 0");
     if (!s->initialised) return fail(ELBM_ERR_STATE, "elbm_step before elbm_init");
-    const int kernel = effective_kernel(s);
+    const int kernel = elbm::effective_kernel(s);
     cudaError_t e = cudaSuccess;
     int left = n;
     while (left > 0 && e == cudaSuccess) {

@@ -77,6 +77,7 @@ struct Solver {
     long long steps_done = 0;
     long long launches = 0;
     size_t bytes = 0;
+    long long uid = 0;                // unique per solver of the process (never reused)
 };
 
 // One member of a batch (see batch.cuh).
@@ -101,6 +102,9 @@ template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 bool single_tmem_geometry(const Solver& s);
+// Kernel form a step of s uses (1 two-pass, 2 graph-pipelined, 3 single pass):
+// the requested form where it applies, else the two-pass form.
+int effective_kernel(const Solver* s);
 template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);

@@ -274,8 +274,11 @@ class Solver:
 
 
 class Batch:
-    """Solvers of one lattice, storage mode and stream advanced together (two
-    launches per step for the whole batch, replayed from a CUDA graph)."""
+    """Solvers of one lattice, storage mode, stream and kernel form advanced
+    together.  Two-pass members: two launches per step for the whole batch,
+    replayed from a CUDA graph.  Single-pass members (kernel=3): each member's
+    step sequence is a CUDA graph of its own, replayed side by side with the
+    others on private streams of the batch."""
 
     def __init__(self, solvers):
         L = load()

@@ -5,11 +5,14 @@ storage mode and number of steps) arrive over time.  The server keeps the
 populations of admitted requests resident on the GPU, admits waiting
 requests whenever the HBM budget and the slot limit allow, and advances all
 resident solves together in chunks of steps with the batched step of the
-library (one CUDA graph of two launches per step for every group of requests
-that share lattice and storage mode).  Requests that arrive while others run
-join at the next chunk boundary; finished ones are read out and freed.  The
-"plain" mode serves the same trace one request at a time in arrival order,
-with per-step launches and no graphs.
+library, one batch for every group of requests that share lattice, storage
+mode and kernel form: D3Q27 grids the single pass takes (x a multiple of 32
+nodes, y of 16) run in it, one CUDA graph per request replayed side by side;
+the others run in the two-pass form, one CUDA graph of two launches per step
+for the whole group.  Requests that arrive while others run join at the next
+chunk boundary; finished ones are read out and freed.  The "plain" mode
+serves the same trace one request at a time in arrival order, in the same
+kernel forms, with per-step launches and no graphs.
 
 Every computation runs in the CUDA library; this module only schedules.
 """
@@ -46,9 +49,19 @@ class Request:
     def cells(self) -> int:
         return self.n[0] * self.n[1] * self.n[2]
 
-    def device_bytes(self) -> int:
-        """Populations (with tail padding) and the anomaly field."""
-        return self.lattice * self.cells * Q_BYTES[self.storage] + 16 + 3 * self.cells * 4
+    @property
+    def single_pass_fits(self) -> bool:
+        """Whether the single-pass form takes this grid (D3Q27, x a multiple
+        of 32 nodes, y of 16, 16-byte aligned rows)."""
+        nx, ny, _ = self.n
+        return (self.lattice == elbm.D3Q27 and nx % 32 == 0 and ny % 16 == 0
+                and (nx * Q_BYTES[self.storage]) % 16 == 0)
+
+    def device_bytes(self, single_pass: bool = False) -> int:
+        """Populations (with tail padding; two arrays in the single-pass form)
+        and the anomaly field."""
+        arrays = 2 if single_pass else 1
+        return arrays * (self.lattice * self.cells * Q_BYTES[self.storage] + 16) + 3 * self.cells * 4
 
 
 def make_trace(n_requests=200, rate=20.0, seed=0, steps=2000, sizes=(32, 48, 64, 96, 128)):
@@ -100,11 +113,12 @@ class _Slot:
     solver: object
     left: int
     t_admit: float
+    form: int = 1
     in_batch: bool = False
 
     @property
     def key(self):
-        return (self.req.lattice, self.req.storage)
+        return (self.req.lattice, self.req.storage, self.form)
 
 
 class Server:
@@ -121,13 +135,19 @@ class Server:
                       that small solves are not held back by large ones while
                       the GPU stays full
     step_floor_nodes  nodes per batched step below which "srpt" adds more requests
+    kernels           "auto": the single-pass form for the grids it takes, the
+                      two-pass form for the rest; "two-pass": the two-pass form
+                      for every request
     clock             callable giving seconds (wall clock by default)
     """
 
     def __init__(self, hbm_budget=8 << 30, chunk_steps=100, max_active=64, clock=time.perf_counter,
-                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=4 << 20):
+                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=4 << 20, kernels="auto"):
         if policy not in ("fifo", "srpt"):
             raise ValueError("policy must be 'fifo' or 'srpt'")
+        if kernels not in ("auto", "two-pass"):
+            raise ValueError("kernels must be 'auto' or 'two-pass'")
+        self.kernels = kernels
         self.hbm_budget = int(hbm_budget)
         self.chunk_steps = int(chunk_steps)
         self.max_active = int(max_active)
@@ -139,9 +159,16 @@ class Server:
         self.results = {}
         self.failed = {}
 
+    def form(self, req):
+        """Kernel form of a request: 3 (single pass) or 1 (two-pass)."""
+        return 3 if self.kernels == "auto" and req.single_pass_fits else 1
+
+    def device_bytes(self, req):
+        return req.device_bytes(single_pass=self.form(req) == 3)
+
     def _start(self, req):
         s = elbm.Solver(req.lattice, req.n, stretch=req.stretch, T=req.T, nu=req.nu, storage=req.storage,
-                        stream=self.stream, kernel=1,
+                        stream=self.stream, kernel=self.form(req),
                         u_ref=req.advection if req.storage != elbm.F32 else None)
         rho, u = initial_field(req)
         s.init(rho, u)
@@ -163,7 +190,8 @@ class Server:
             order = sorted(order, key=lambda i: (queue[i].cells * queue[i].steps, queue[i].arrival))
         for i in order:
             req = queue[i]
-            fits = used + req.device_bytes() <= self.hbm_budget and kinds[(req.lattice, req.storage)] < BATCH_MAX
+            fits = (used + self.device_bytes(req) <= self.hbm_budget
+                    and kinds[(req.lattice, req.storage, self.form(req))] < BATCH_MAX)
             if fits:
                 return i
             if self.policy == "fifo":
@@ -203,7 +231,7 @@ class Server:
         queue = []
         active = []           # _Slot of every resident request
         used = 0
-        batches = {}          # (lattice, storage) -> Batch of the stepping members of that kind
+        batches = {}          # (lattice, storage, form) -> Batch of the stepping members of that kind
         while pending or queue or active:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
@@ -222,14 +250,15 @@ class Server:
                         self.failed[req.rid] = str(err)
                     break  # out of memory while others run: retry once some finish
                 queue.pop(i)
-                used += req.device_bytes()
-                kinds[(req.lattice, req.storage)] += 1
-                active.append(_Slot(req, solver, req.steps, self.clock() - t0))
+                used += self.device_bytes(req)
+                slot = _Slot(req, solver, req.steps, self.clock() - t0, self.form(req))
+                kinds[slot.key] += 1
+                active.append(slot)
             if not active:
-                if queue and all(used + r.device_bytes() > self.hbm_budget for r in queue):
+                if queue and all(used + self.device_bytes(r) > self.hbm_budget for r in queue):
                     req = min(queue, key=lambda r: r.arrival)  # larger than the whole budget
                     queue.remove(req)
-                    self.failed[req.rid] = f"needs {req.device_bytes()} bytes, budget {self.hbm_budget}"
+                    self.failed[req.rid] = f"needs {self.device_bytes(req)} bytes, budget {self.hbm_budget}"
                     continue
                 if pending and not queue:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
@@ -261,7 +290,7 @@ class Server:
                     batches[a.key].remove(a.solver)
                     a.in_batch = False
                     self._finish(a.req, a.solver, t0, a.t_admit)
-                    used -= a.req.device_bytes()
+                    used -= self.device_bytes(a.req)
                 else:
                     still.append(a)
             active = still

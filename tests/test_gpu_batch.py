@@ -96,3 +96,80 @@ def test_members_join_and_leave_a_running_batch():
         assert np.array_equal(s.get_populations(), m.get_populations())
     for s in solo + mixed:
         s.close()
+
+
+# single-pass members (kernel 3): x a multiple of 32 nodes and y of 16 for the TMEM form
+SPECS_SP = [((32, 32, 32), (1.0, 1.0, 1.0), 1 / 3, 0.02), ((64, 32, 64), (1.0, 2.0, 1.0), 0.6, 0.015),
+            ((96, 48, 40), (1.0, 1.5, 2.0), 0.45, 0.01), ((64, 16, 7), (1.0, 1.0, 1.0), 0.5, 0.03)]
+
+
+def _make_sp(spec, storage, seed, **kw):
+    n, lam, T, nu = spec
+    s = elbm.Solver(elbm.D3Q27, n, stretch=lam, T=T, nu=nu, storage=storage, kernel=3,
+                    stream=torch.cuda.current_stream(), **kw)
+    s.init(*_fields(n, seed, 3))
+    return s
+
+
+@pytest.mark.parametrize("storage", [elbm.F32_SHIFT, elbm.F16_SHIFT])
+def test_single_pass_batch_matches_solo_bitwise(storage):
+    """Single-pass members of different sizes and parameters, with an odd step
+    count (the arrays swap) and a repeated one (the cached graphs replay):
+    bit for bit the states of stepping each alone."""
+    solo = [_make_sp(sp, storage, k) for k, sp in enumerate(SPECS_SP)]
+    mixed = [_make_sp(sp, storage, k) for k, sp in enumerate(SPECS_SP)]
+    for s in solo:
+        s.step(27)
+    with elbm.Batch(mixed) as b:
+        b.step(7)
+        b.step(10)
+        b.step(10)
+        info = b.info()
+    assert info["block_size"] == 0 and info["launches"] == 27 * len(SPECS_SP)
+    for s, m in zip(solo, mixed):
+        assert m.steps_done == s.steps_done == 27
+        assert np.array_equal(s.get_populations(), m.get_populations())
+
+
+def test_single_pass_batch_membership_and_bounded_members():
+    """Members leave and join between steps (a leaving member's graphs are
+    released), a wall-bounded, forced channel member runs beside periodic ones,
+    and every state equals the solo run; two-pass and single-pass members do
+    not share a batch."""
+    chan = ((64, 32, 20), (2.0, 1.0, 2.0), 0.55, 0.02)
+    rho_c, u_c = inputs.channel(chan[0], chan[1], u_center=0.05, perturbation=0.05, seed=3)
+
+    def make_chan():
+        s = elbm.Solver(elbm.D3Q27, chan[0], stretch=chan[1], T=chan[2], nu=chan[3], storage=elbm.F32, kernel=3,
+                        walls_y=True, force=(2e-5, 0.0, 0.0), stream=torch.cuda.current_stream())
+        s.init(rho_c, u_c)
+        return s
+
+    specs = SPECS_SP[:3]
+    solo = [_make_sp(sp, elbm.F32, k) for k, sp in enumerate(specs)] + [make_chan()]
+    mixed = [_make_sp(sp, elbm.F32, k) for k, sp in enumerate(specs)] + [make_chan()]
+    steps = [0] * 4
+    with elbm.Batch([mixed[0], mixed[3]]) as b:
+        b.step(5)
+        steps[0] += 5; steps[3] += 5
+        b.add(mixed[1])
+        b.add(mixed[2])
+        b.step(4)
+        for k in range(4):
+            steps[k] += 4
+        b.remove(mixed[0])
+        b.step(5)
+        for k in (1, 2, 3):
+            steps[k] += 5
+        b.add(mixed[0])
+        b.step(4)
+        for k in range(4):
+            steps[k] += 4
+        assert len(b) == 4
+        with pytest.raises(elbm.ElbmError):
+            b.add(_make(elbm.D3Q27, SPECS3[0], elbm.F32, 9))  # a two-pass member
+    for s, k in zip(solo, steps):
+        s.step(k)
+    for s, m in zip(solo, mixed):
+        assert m.steps_done == s.steps_done
+        assert np.array_equal(s.get_populations(), m.get_populations())

@@ -29,6 +29,8 @@ class World:
         self.live = {}
         self.peak_bytes = 0
         self.batch_log = []
+        self.batch_kernels = []
+        self.kernels = {}
 
     def solver_cls(self, server):
         world = self
@@ -38,8 +40,9 @@ class World:
                 req = server._current
                 if req.rid in world.fail_rids:
                     raise elbm.ElbmError(-3, "injected out of memory")
-                self.req, self.steps_done, self.N = req, 0, n[0] * n[1] * n[2]
-                world.live[id(self)] = req.device_bytes()
+                self.req, self.steps_done, self.N, self.kernel = req, 0, n[0] * n[1] * n[2], kernel
+                world.kernels[req.rid] = kernel
+                world.live[id(self)] = server.device_bytes(req)
                 world.peak_bytes = max(world.peak_bytes, sum(world.live.values()))
 
             def init(self, rho, u):
@@ -75,6 +78,7 @@ class World:
 
             def step(self, k):
                 world.batch_log.append(tuple(s.req.rid for s in self.solvers))
+                world.batch_kernels.append(set(s.kernel for s in self.solvers))
                 for s in self.solvers:
                     s.steps_done += k
                 world.clock.t += k * sum(s.N for s in self.solvers) * 1e-9 / 4  # batching fills the GPU
@@ -85,10 +89,11 @@ class World:
         return FakeBatch
 
 
-def serve_fake(monkeypatch, trace, budget, fail_rids=(), mode="batched", chunk=50, policy="fifo", floor=4 << 20):
+def serve_fake(monkeypatch, trace, budget, fail_rids=(), mode="batched", chunk=50, policy="fifo", floor=4 << 20,
+               kernels="auto"):
     clock = FakeClock()
     server = serve.Server(hbm_budget=budget, chunk_steps=chunk, clock=clock, sleep=clock.sleep, policy=policy,
-                          step_floor_nodes=floor)
+                          step_floor_nodes=floor, kernels=kernels)
     world = World(clock, fail_rids)
     orig_start = server._start
 
@@ -177,3 +182,39 @@ def test_srpt_lets_small_requests_pass_a_large_one(monkeypatch):
         assert stepped >= floor or len(ids) == len(set(ids))
     fifo_server, fifo_summary, _ = serve_fake(monkeypatch, trace, budget=1 << 40, policy="fifo")
     assert summary["p50_latency_s"] < fifo_summary["p50_latency_s"]
+
+
+def test_single_pass_fit_and_bytes():
+    """The single-pass form takes D3Q27 grids with x a multiple of 32 nodes and
+    y of 16, and holds two population arrays."""
+    base = serve.make_trace(1, seed=0)[0]
+    fits = {n: dataclasses.replace(base, n=n).single_pass_fits
+            for n in [(32, 32, 32), (48, 48, 48), (64, 32, 64), (96, 96, 96), (128, 128, 128), (64, 40, 64)]}
+    assert fits == {(32, 32, 32): True, (48, 48, 48): False, (64, 32, 64): True, (96, 96, 96): True,
+                    (128, 128, 128): True, (64, 40, 64): False}
+    r = dataclasses.replace(base, n=(64, 64, 64), storage=elbm.F16_SHIFT)
+    pop = 27 * 64 ** 3 * 2 + 16
+    assert r.device_bytes() == pop + 3 * 64 ** 3 * 4
+    assert r.device_bytes(single_pass=True) == 2 * pop + 3 * 64 ** 3 * 4
+
+
+@pytest.mark.parametrize("policy", ["fifo", "srpt"])
+def test_kernel_forms_per_grid_and_batches_never_mix_them(monkeypatch, policy):
+    """"auto" runs the grids the single pass takes in it (kernel 3) and the rest
+    in the two-pass form (kernel 1), in separate batches; "two-pass" runs every
+    request in the two-pass form; plain mode chooses as "auto" does."""
+    trace = serve.make_trace(40, seed=11, steps=200, rate=200.0)
+    server, summary, world = serve_fake(monkeypatch, trace, budget=1 << 40, policy=policy, floor=1 << 20)
+    assert summary["served"] == 40
+    assert all(world.kernels[r.rid] == (3 if r.single_pass_fits else 1) for r in trace)
+    assert {1, 3} <= set(world.kernels.values())
+    assert world.batch_kernels and all(len(k) == 1 for k in world.batch_kernels)
+    _, summary2, world2 = serve_fake(monkeypatch, trace, budget=1 << 40, policy=policy, kernels="two-pass")
+    assert summary2["served"] == 40 and set(world2.kernels.values()) == {1}
+    _, _, world3 = serve_fake(monkeypatch, trace[:6], budget=1 << 40, mode="plain")
+    assert all(world3.kernels[r.rid] == (3 if r.single_pass_fits else 1) for r in trace[:6])
+
+
+def test_unknown_kernel_choice_is_rejected():
+    with pytest.raises(ValueError):
+        serve.Server(kernels="single")
