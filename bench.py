@@ -55,7 +55,9 @@ MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47
                     ("8b7c40bddffd89cf", "f32s", 3): 3.646e9,
                     ("93127f9738070902", "f32s", 3): 3.647e9,
                     # 217.0 B/node measured at 192^3 with one FP32 tile buffer and plain stores, x 256^3
-                    ("15ce62cad8a5ee9a", "f32s", 3): 3.640e9}
+                    ("15ce62cad8a5ee9a", "f32s", 3): 3.640e9,
+                    # 217.15 B/node at 192^3 with the moments and increment sums grouped along lattice lines, x 256^3
+                    ("90b4bc70690322b5", "f32s", 3): 3.643e9}
 
 
 def kernel_source_hash() -> str:
@@ -253,7 +255,7 @@ def serve_arm(args):
                                             "requests": len(trace), "hbm_budget_GiB": 8, "chunk_steps": 100},
             "batched": batched, "batched_fifo": batched_fifo, "plain": plain,
             "batched_two_pass": batched_two_pass, "plain_two_pass": plain_two_pass,
-            "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 4 Mi nodes",
+            "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 8 Mi nodes",
             "kernels": "single pass for grids with x % 32 == 0 and y % 16 == 0 (one graph per solve, run side "
                        "by side), two-pass batched kernels for the rest; *_two_pass: two-pass for every solve",
             # against the faster one-at-a-time service (alone, a small grid fills the GPU better in the

@@ -47,19 +47,23 @@ __global__ void __launch_bounds__(kBlock) k_anomaly(StepParams p)
 template <int D, typename G>
 __device__ __forceinline__ void moments_of(const StepParams& p, G&& gval, float& drho, float* j)
 {
-    float r = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+    // lines of three along x (population index x fastest), then rows along y, then planes along z
+    constexpr int NL = Lat<D>::Q / 3, NP = NL / 3 > 0 ? NL / 3 : 1;
+    float t[NL], sx = 0.f, sy = 0.f;
 #pragma unroll
-    for (int i = 0; i < Lat<D>::Q; ++i) {
-        const float gi = gval(i);
-        r += gi;
-        if (cx_of(i) == 1) sx += gi;
-        if (cx_of(i) == -1) sx -= gi;
-        if (cy_of(i) == 1) sy += gi;
-        if (cy_of(i) == -1) sy -= gi;
-        if (cz_of<D>(i) == 1) sz += gi;
-        if (cz_of<D>(i) == -1) sz -= gi;
+    for (int L = 0; L < NL; ++L) {
+        const float a = gval(3 * L), b = gval(3 * L + 1), c = gval(3 * L + 2);
+        t[L] = (a + b) + c;
+        sx += c - a;
     }
-    drho = r;
+    float tp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int P = 0; P < NP; ++P) {
+        tp[P] = (t[3 * P] + t[3 * P + 1]) + t[3 * P + 2];
+        sy += t[3 * P + 2] - t[3 * P];
+    }
+    drho = (D == 3) ? (tp[0] + tp[1]) + tp[2] : tp[0];
+    const float sz = (D == 3) ? tp[2] - tp[0] : 0.f;
     j[0] = fmaf(p.lam[0], sx, p.j0[0]);
     j[1] = fmaf(p.lam[1], sy, p.j0[1]);
     j[2] = (D == 3) ? fmaf(p.lam[2], sz, p.j0[2]) : 0.f;
@@ -92,16 +96,31 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     if (forced) frc.init(p, rho / om, u);
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
     float keep[2 * D + 1], kf[2 * D + 1];
+    // the increments' moments, summed along the enumeration's lines: cz
+    // innermost (D3Q27) or cx innermost (D2Q9), then cx, then cy
+    float line[3], row[3];
+    auto accumulate = [&](int i, float dl) {
+        const int cx = cx_of(i), cy = cy_of(i);
+        if (D == 3) {
+            const int cz = cz_of<D>(i);
+            line[cz + 1] = dl;
+            if (cz != 1) return;
+            row[cx + 1] = (line[0] + line[1]) + line[2];
+            ez += line[2] - line[0];
+        } else {
+            row[cx + 1] = dl;
+        }
+        if (cx != 1) return;
+        const float rs = (row[0] + row[1]) + row[2];
+        ex += row[2] - row[0];
+        e0 += rs;
+        if (cy == 1) ey += rs;
+        if (cy == -1) ey -= rs;
+    };
     auto relax_one = [&](int i, float geq) {
         const float gi = gval(i);
         const float dl = geq - gi;
-        e0 += dl;
-        if (cx_of(i) == 1) ex += dl;
-        if (cx_of(i) == -1) ex -= dl;
-        if (cy_of(i) == 1) ey += dl;
-        if (cy_of(i) == -1) ey -= dl;
-        if (cz_of<D>(i) == 1) ez += dl;
-        if (cz_of<D>(i) == -1) ez -= dl;
+        accumulate(i, dl);
         const int k = corrected_slot<D>(i);
         if (k >= 0) {
             keep[k] = geq;

@@ -142,7 +142,7 @@ class Server:
     """
 
     def __init__(self, hbm_budget=8 << 30, chunk_steps=100, max_active=64, clock=time.perf_counter,
-                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=4 << 20, kernels="auto"):
+                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=8 << 20, kernels="auto"):
         if policy not in ("fifo", "srpt"):
             raise ValueError("policy must be 'fifo' or 'srpt'")
         if kernels not in ("auto", "two-pass"):
