@@ -9,14 +9,16 @@
 //     shared memory, and the ring of nodes around the tile -- two TMA row
 //     boxes and two columns of 16 nodes by cp.async -- into a ring of two
 //     buffers; one mbarrier per buffer ("full") tracks both kinds of copy.
-//     The other warps of warpgroup 4 only fill it up: TMEM lane quarters
-//     follow a warp's rank within its warpgroup, so the consumers must make
-//     whole warpgroups;
+//     With 16-bit storage its other three warps compute the anomaly of the
+//     ring (the row below, the row above, the two columns); with FP32 storage
+//     they idle (TMEM lane quarters follow a warp's rank within its
+//     warpgroup, so the consumers must make whole warpgroups) and the
+//     consumers share the ring out;
 //   * the 16 warps of warpgroups 0..3 each own one tile row.  For plane k a
 //     thread reads its node's 27 populations from shared memory once, hands
 //     the buffer back ("empty" mbarrier), parks the values in its TMEM lane,
-//     computes the anomaly Q~ of its node and of a share of the ring (the duty
-//     rotates over the warps from plane to plane), publishes them ("qready")
+//     computes the anomaly Q~ of its node (FP32 storage: and of a share of the
+//     ring, the duty rotating over the warps from plane to plane), publishes it ("qready")
 //     and relaxes plane k-1 -- with the values parked one plane earlier --
 //     once every warp has published the anomaly of plane k-1 (the central
 //     difference of Eq. Paastar1 needs the face neighbours), pushing the 27
@@ -46,6 +48,10 @@ struct TmemLayout {
     using T = typename Storage<ST>::T;
     static constexpr int es = (int)sizeof(T);
     static constexpr int ntile = es == 4 ? 1 : 2;                    // tile buffers
+    // threads that compute the ring's anomaly apart from the consumers: for
+    // 16-bit storage (issue-bound) the three spare warps of the loading
+    // warpgroup; for FP32 (latency-bound) the consumers share it out
+    static constexpr int ring_threads = es == 4 ? 0 : 96;
     static constexpr int tile_bytes = 27 * kTmTileY * kTileX * es;   // one plane of the tile
     static constexpr int row_box_bytes = 27 * kTileX * es;           // one ring row, all populations
     static constexpr int row_stride = (row_box_bytes + 127) / 128 * 128;
@@ -103,9 +109,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
         }
         for (int r = 0; r < 2; ++r) {
             mbar_init(full_r(r), 1 + 32);  // loader lane 0 (expect_tx) + the cp.async arrivals of its 32 lanes
-            mbar_init(empty_r(r), kTmConsumers);
+            mbar_init(empty_r(r), kTmConsumers + L::ring_threads);
         }
-        for (int s = 0; s < kTmaQSlots; ++s) mbar_init(qready(s), kTmConsumers);
+        for (int s = 0; s < kTmaQSlots; ++s) mbar_init(qready(s), kTmConsumers + L::ring_threads);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -162,6 +168,45 @@ __global__ void __launch_bounds__(kTmThreads, 1)
                 for (int k = max(0, issued - 2); k < issued; ++k) drain(full_r(k & 1), (k / 2) & 1);
             }
             __syncwarp();
+        } else if (L::ring_threads > 0) {
+            // ------------------------------------------------ ring anomaly
+            // warp 1 of the group: the row below the tile, warp 2: the row
+            // above, warp 3: the two columns (nodes x0-1 and x0+32 of the tile's rows)
+            const int duty = warp - kLoader - 1;
+            auto anomaly_of = [&](auto&& gval, float* q) {
+                float drho, j[3];
+                moments_of<3>(p, gval, drho, j);
+                const float inv_rho = 1.0f / (p.rho_ref + drho);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) q[a] = anomaly(p, a, j[a], j[a] * inv_rho);
+            };
+            float* qxs = reinterpret_cast<float*>(base + L::off_qx);
+            float* qys = reinterpret_cast<float*>(base + L::off_qy);
+            for (int k = 0; k < K; ++k) {
+                const int r = k & 1, s = k % kTmaQSlots;
+                if (!__all_sync(0xffffffffu, wait(full_r(r), (k / 2) & 1))) break;
+                if (k > 0 && k < K - 1) {
+                    float qh[3];
+                    if (duty < 2) {
+                        const T* row =
+                            reinterpret_cast<const T*>(base + L::off_rows + (2 * r + duty) * L::row_stride) + lane;
+                        anomaly_of([&](int i) { return raw_value<ST>(p, row[i * kTileX], i); }, qh);
+                        qys[(s * (kTmTileY + 2) + (duty ? kTmTileY + 1 : 0)) * kTileX + lane] = qh[1];
+                    } else {
+                        const unsigned* cols =
+                            reinterpret_cast<const unsigned*>(base + L::off_cols + r * L::cols_bytes) + lane;
+                        const int cx = lane < kTmTileY ? wrapi(x0 - 1, p.nx) : wrapi(x0 + kTileX, p.nx);
+                        const int idx0 = plane_of(k) * p.plane + (y0 + (lane & (kTmTileY - 1))) * p.nx + cx;
+                        anomaly_of([&](int i) { return stage_value<ST>(p, cols[i * L::ncol], (i * p.N + idx0) & 1, i); },
+                                   qh);
+                        qxs[(s * kTmTileY + (lane & (kTmTileY - 1))) * (kTileX + 2) + (lane < kTmTileY ? 0 : kTileX + 1)] =
+                            qh[0];
+                    }
+                }
+                __syncwarp();
+                mbar_arrive(empty_r(r));
+                mbar_arrive(qready(s));
+            }
         }
     } else {
         // ------------------------------------------------------ consumers
@@ -212,7 +257,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             // ring share of this warp for plane k (duty rotates with k): 0 the
             // row below the tile, 1 the row above, 2 the two columns
             const int duty = (ty + k) & (kTmTileY - 1);
-            if (k > 0 && k < K - 1) {
+            if (L::ring_threads == 0 && k > 0 && k < K - 1) {
                 if (duty < 2) {
                     const T* row = reinterpret_cast<const T*>(base + L::off_rows + (2 * r + duty) * L::row_stride) + tx;
                     float qh[3];
