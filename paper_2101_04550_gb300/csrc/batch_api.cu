@@ -196,6 +196,9 @@ cudaError_t ensure_pool(elbm_batch* b, int n)
 // batch's stream, launch each member's graph on one of them, join them back.
 int step_single_form(elbm_batch* b, int nsteps)
 {
+    for (const auto* s : b->members)
+        if (member_form(s) != 3 || s->parity != 0 || !s->f2)
+            return bfail(ELBM_ERR_STATE, "a member of a single-pass batch no longer steps in the single-pass form");
     reap(b, false);
     const int n = (int)b->members.size(), P = std::min(n, kPoolStreams);
     cudaError_t e = ensure_pool(b, P);
