@@ -38,3 +38,15 @@ def test_two_gloo_ranks_use_the_slowest_time():
 def test_single_rank_is_unchanged():
     assert bench.max_over_ranks(0.5, None) == 0.5
     assert bench.aggregate_mlups(1, 1000, 10, 0.01) == pytest.approx(1.0)
+
+
+def test_kernel_source_hash_covers_existing_files():
+    """The sources bench.py hashes to key its measured traffic all exist, and
+    the hash is a stable 16-digit hex string."""
+    import os
+    import bench
+    for rel in bench.KERNEL_SOURCES:
+        root = bench.ROOT if rel.startswith("include/") else os.path.join(bench.ROOT, "paper_2101_04550_gb300")
+        assert os.path.isfile(os.path.join(root, rel)), rel
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0 and h == bench.kernel_source_hash()
