@@ -73,10 +73,17 @@ extern "C" {
 #define ELBM_OPT_EQUILIBRIUM 1
 /* ELBM_OPT_KERNEL: the form of the step; every form evaluates the same per-node
  *   arithmetic and gives bit-identical results.
- *   0 = automatic (the two-pass form);
+ *   0 = automatic (the default): the single pass (form 3, TMEM kernel) on
+ *       D3Q27 grids with nx a multiple of 32 and ny of 16, for which
+ *       elbm_create (or setting this option) then allocates the second
+ *       population array -- twice the population memory; if that allocation
+ *       fails the solver keeps one array and steps in the two-pass form.
+ *       Every other grid, D2Q9, and the second-order equilibrium: the
+ *       two-pass form.  elbm_kernel_form() reports the choice;
  *   1 = two-pass, in place: an anomaly pass over the grid, then the collide pass;
  *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide
  *       kernels, so that the collide kernels re-read populations from L2;
+ *       forms 1 and 2 release a second population array if one is held;
  *   3 = single pass with a second population array (D3Q27 only): every block
  *       recomputes the anomaly around its tile and reads the populations once
  *       (TMA-fed, populations parked in tensor memory, when nx is a multiple
@@ -195,6 +202,13 @@ int elbm_mode_sums(elbm_solver* s, const double* k, const double* dir, double* o
 
 /* Block the host until the solver's stream is idle. */
 int elbm_sync(elbm_solver* s);
+
+/* Kernel form the next elbm_step of s uses: 1 two-pass, 2 graph-pipelined,
+ * 3 single pass (ELBM_OPT_KERNEL and the grid decide it; see there), or
+ * ELBM_ERR_ARG for NULL.  For form 3, *variant (if not NULL) receives the
+ * single-pass kernel: 1 TMEM (32 x 16 tiles), 2 TMA (32 x 8 tiles),
+ * 3 cp.async-staged; 0 for the other forms.  Host-side query, no CUDA call. */
+int elbm_kernel_form(const elbm_solver* s, int* variant);
 
 /* Informational queries. */
 long long elbm_cells(const elbm_solver* s);

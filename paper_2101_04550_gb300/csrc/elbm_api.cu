@@ -127,13 +127,15 @@ void fill_params(const Solver& s, StepParams& p)
     p.parity = s.parity;
 }
 
-// Kernel form a step uses: 0 (automatic) means the two-pass form, which is
-// also the only form of the second-order equilibrium.
-// The second-order equilibrium runs in the two-pass form; walls and the body
-// force in the two-pass form or, where its geometry allows, the TMEM single pass.
+// Kernel form a step uses.  Automatic (0): the TMEM single pass on the D3Q27
+// grids it takes (x a multiple of 32 nodes, y of 16) once its second
+// population array has been allocated, the two-pass form otherwise.  The
+// second-order equilibrium runs in the two-pass form; walls and the body force
+// in the two-pass form or, where its geometry allows, the TMEM single pass.
 int effective_kernel(const Solver* s)
 {
-    if (s->kernel == 0 || s->eq_mode == 2) return 1;
+    if (s->eq_mode == 2) return 1;
+    if (s->kernel == 0) return (s->f2 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
     const bool bounded = s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
     if (!bounded) return s->kernel;
     return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
@@ -178,14 +180,30 @@ size_t population_bytes(const elbm_solver* s)
     return (size_t)s->Q * s->N * elbm::storage_bytes(s->storage) + 16;
 }
 
-// The single-pass form needs a second population array.
+// The single-pass form needs a second population array.  Requested
+// explicitly (kernel 3), a failed allocation is an error; for the automatic
+// form (kernel 0) on a grid the TMEM single pass takes it is an attempt, and
+// without the array the solver steps in the two-pass form.  The in-place forms
+// (1, 2) release it: the current state always sits in s->f.
 int ensure_second_array(elbm_solver* s, int kernel)
 {
-    const int k = kernel != 0 ? kernel : 1;
-    if (k != 3 || s->f2) return ELBM_OK;
+    if (kernel == 1 || kernel == 2) {
+        if (s->f2) {
+            cudaFreeAsync(s->f2, s->stream);  // stream-ordered: after the queued steps that use it
+            s->f2 = nullptr;
+            s->bytes -= population_bytes(s);
+        }
+        return ELBM_OK;
+    }
+    if (s->f2) return ELBM_OK;
+    if (kernel == 0 && !elbm::single_tmem_geometry(*s)) return ELBM_OK;
     cudaError_t e = cudaMallocAsync(&s->f2, population_bytes(s), s->stream);
     if (e != cudaSuccess) {
         s->f2 = nullptr;
+        if (kernel == 0) {
+            (void)cudaGetLastError();  // the automatic form falls back to the two-pass form
+            return ELBM_OK;
+        }
         return cuda_fail(e, "second population array");
     }
     s->bytes += population_bytes(s);
@@ -578,6 +596,15 @@ int elbm_mode_sums(elbm_solver* s, const double* k, const double* dir, double* o
     out[0] = s->host_red[0];
     out[1] = s->host_red[1];
     return check_status(s);
+}
+
+int elbm_kernel_form(const elbm_solver* s, int* variant)
+{
+    if (variant) *variant = 0;
+    if (!s) return fail(ELBM_ERR_ARG, "solver is NULL");
+    const int form = elbm::effective_kernel(s);
+    if (form == 3 && variant) *variant = elbm::single_pass_variant(*s);
+    return form;
 }
 
 long long elbm_cells(const elbm_solver* s) { return s ? s->N : 0; }

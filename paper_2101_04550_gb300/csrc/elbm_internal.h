@@ -102,6 +102,7 @@ template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 bool single_tmem_geometry(const Solver& s);
+int single_pass_variant(const Solver& s);
 // Kernel form a step of s uses (1 two-pass, 2 graph-pipelined, 3 single pass):
 // the requested form where it applies, else the two-pass form.
 int effective_kernel(const Solver* s);

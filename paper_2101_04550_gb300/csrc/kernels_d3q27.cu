@@ -22,4 +22,14 @@ bool single_tmem_geometry(const Solver& s)
 {
     return s.D == 3 && s.nx % kTileX == 0 && s.ny % kTmTileY == 0 && (s.nx * (int)storage_bytes(s.storage)) % 16 == 0;
 }
+// Single-pass kernel a step of s launches (the arrays are 16-byte aligned, as
+// the stream-ordered allocator returns them): 1 TMEM (32 x 16 tiles), 2 TMA
+// (32 x 8 tiles), 3 cp.async-staged.  Walls and the body force run in the
+// TMEM kernel only.
+int single_pass_variant(const Solver& s)
+{
+    if (single_tmem_geometry(s)) return 1;
+    const bool fast = s.nx % kTileX == 0 && s.ny % kTileY == 0 && (s.nx * (int)storage_bytes(s.storage)) % 16 == 0;
+    return fast ? 2 : 3;
+}
 }  // namespace elbm

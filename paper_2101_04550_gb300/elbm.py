@@ -36,7 +36,7 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
            "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
-           "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums"]
+           "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums", "elbm_kernel_form"]
 
 
 class ElbmError(RuntimeError):
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
         L.elbm_batch_step.argtypes = [vp, ip]
         L.elbm_selftest_wait_timeout.argtypes = [ip, vp]
         L.elbm_mode_sums.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)]
+        L.elbm_kernel_form.argtypes = [vp, ctypes.POINTER(ip)]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
         L.elbm_batch_add.argtypes = [vp, vp]
         L.elbm_batch_remove.argtypes = [vp, vp]
@@ -251,6 +252,16 @@ class Solver:
         out = (ctypes.c_double * 3)()
         _check(load().elbm_get_u_ref(self._h, out))
         return tuple(out)[: self.D]
+
+    @property
+    def kernel_form(self):
+        """(form, variant) of the next step: form 1 two-pass, 2 graph-pipelined,
+        3 single pass; variant (form 3) 1 TMEM, 2 TMA, 3 cp.async-staged."""
+        v = ctypes.c_int()
+        form = load().elbm_kernel_form(self._h, ctypes.byref(v))
+        if form < 0:
+            _check(form)
+        return form, v.value
 
     @property
     def omega(self):

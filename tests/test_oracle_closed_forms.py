@@ -173,3 +173,64 @@ def test_central_difference_second_order():
         # along y the field is constant, the difference vanishes
         assert np.abs(o.central_difference(q, 1)).max() == 0.0
     assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2
+
+
+def truncated_moment(orders, u, T, lam, D):
+    """Moment sum_i rho^-1 prod_a (lam_a c_ia)^(l_a) f_i of the second-order
+    equilibrium (Sec. III preamble) in closed form.  Per axis the product form
+    has the moments 1, u_a, T + u_a^2 (Sec. II.B: M_100 = u, M_200 = P with
+    P = T + u^2); a moment of the product is the product of the per-axis
+    moments, and dropping every term above second order in u from the
+    populations drops the same terms from each moment, because the moment sum
+    does not mix powers of u.  So the moment is the product of the per-axis
+    polynomials with every term of total degree above two removed."""
+    # per-axis polynomial in u_a: coefficients of u_a^0, u_a^1, u_a^2
+    per_axis = {0: (1.0, 0.0, 0.0), 1: (0.0, 1.0, 0.0), 2: (T, 0.0, 1.0)}
+    total = 0.0
+    for powers in itertools.product(range(3), repeat=D):
+        if sum(powers) > 2:
+            continue
+        term = 1.0
+        for a in range(D):
+            term *= per_axis[orders[a]][powers[a]] * u[a] ** powers[a]
+        total += term
+    return total
+
+
+@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("trial", range(6))
+def test_second_order_equilibrium_moments_general_T_lambda(D, trial):
+    """The second-order equilibrium at random stretch lam in [0.7, 2.2] and
+    T in (0.2, 0.6) (Sec. III preamble, Eqs. Peq, Qeq): all 3^D moments with
+    orders <= 2 per axis -- which fix the 3^D populations -- equal their closed
+    forms.  So rho, rho u and the pressure rho (T I + u u) are kept exactly,
+    the diagonal third moment is rho lam_a^2 u_a (c^3 = c on the lattice), and
+    the off-diagonal Q_abb loses exactly rho u_a u_b^2 against the product form."""
+    rng = np.random.default_rng(1000 + 10 * D + trial)
+    lam = np.array([rng.uniform(0.7, 2.2) for _ in range(3)])
+    T = rng.uniform(0.2, 0.6) * min(1.0, float(np.min(lam[:D] ** 2)))
+    u = np.array([rng.uniform(-0.2, 0.2) for _ in range(3)])
+    if D == 2:
+        u[2] = 0.0
+    rho = rng.uniform(0.8, 1.2)
+    c = table(D)
+    v = c * lam
+    f2 = oracle.equilibrium(D, rho, u, T, lam, second_order=True)
+    for orders in itertools.product(range(3), repeat=D):
+        m = (f2 * np.prod([v[:, a] ** orders[a] for a in range(D)], axis=0)).sum()
+        want = rho * truncated_moment(orders, u, T, lam, D)
+        assert abs(m - want) <= 1e-14 * max(1.0, abs(want)), (orders, m, want)
+    # the named tensors, spelled out
+    mom = lambda w: (f2 * w).sum()
+    assert np.isclose(mom(np.ones(len(c))), rho, rtol=1e-15)
+    for a in range(D):
+        assert np.isclose(mom(v[:, a]), rho * u[a], rtol=0, atol=1e-15)
+        assert np.isclose(mom(v[:, a] ** 3), rho * lam[a] ** 2 * u[a], rtol=0, atol=1e-14)
+        for b in range(D):
+            want_p = rho * ((T if a == b else 0.0) + u[a] * u[b])
+            assert np.isclose(mom(v[:, a] * v[:, b]), want_p, rtol=0, atol=1e-14)
+            if a != b:
+                feq = oracle.equilibrium(D, rho, u, T, lam)
+                q_full = (feq * v[:, a] * v[:, b] ** 2).sum()
+                q_trunc = mom(v[:, a] * v[:, b] ** 2)
+                assert np.isclose(q_full - q_trunc, rho * u[a] * u[b] ** 2, rtol=0, atol=1e-14)
