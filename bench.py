@@ -10,6 +10,13 @@ advances its own independent grid (the workload partitions into independent
 solves, no collective on the data path): ``value`` is the sum over ranks of
 node updates divided by the slowest rank's time.
 
+The line also carries, measured in the same run: the other kernel forms and
+storage modes (``variants``), the D2Q9 double shear layer and the channel
+configurations, the served mix of independent solves batched against one at a
+time (``served``), and the error of the timed configuration against the FP64
+oracle (``accuracy``; the oracle runs in worker processes on the host cores
+while the GPU is timed).
+
 ``--impl reference`` times the FP64 CPU oracle instead, on a bounded slab of the
 same workload, on the host cores.
 """
@@ -42,17 +49,17 @@ CHANNEL = dict(workload="D3Q27 turbulent channel 512x128x256, lam=(2,1,2), walls
 CHANNEL.update(nu=CHANNEL["u_tau"] * 64 / 180.0, g=CHANNEL["u_tau"] ** 2 / 64)
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
-KERNEL_NAMES = {0: "two-pass", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
-KERNEL_LAUNCHES = {0: "k_anomaly+k_collide", 1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range",
-                   3: "k_single_pass_tmem"}
+KERNEL_NAMES = {0: "automatic", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
+KERNEL_LAUNCHES = {1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range", 3: "k_single_pass_tmem"}
 # ncu DRAM bytes (read + write) of one step of the timed kernel form, keyed by
-# the hash of the kernel sources they were measured on, the storage and the form.
-# Entries before "eaf58f1ee0e1b8b6" hash every file of csrc/; later ones the
-# KERNEL_SOURCES below.
-# Two-pass: 339 B/node measured at 192^3 (profiles/k_anomaly_k_collide_d3q27_hit192_f32.md),
+# the hash of the kernel sources they were measured on, the storage and the form
+# (the form as it ran: 0, automatic, ran the two-pass form before that choice
+# moved to the single pass).  Entries before "eaf58f1ee0e1b8b6" hash every file
+# of csrc/; later ones the KERNEL_SOURCES below.
+# Two-pass: 339 B/node measured at 192^3 with the two-pass form's ncu capture,
 # scaled to the 256^3 step: 339.1 * 256^3 bytes.
 MEASURED_TRAFFIC = {("36d3ed5701ac3c47", "f32s", 0): 5.689e9, ("36d3ed5701ac3c47", "f32s", 1): 5.689e9,
-                    # 218.5 B/node measured at 192^3 (profiles/k_single_pass_tmem_d3q27_hit192_f32.md) x 256^3
+                    # 218.5 B/node measured at 192^3 with the single pass's ncu capture, x 256^3
                     ("ea6c7fce23e1af60", "f32s", 3): 3.666e9,
                     # 217.3 B/node measured at 192^3 with the TMA-store form, x 256^3
                     ("8b7c40bddffd89cf", "f32s", 3): 3.646e9,
@@ -186,6 +193,31 @@ def time_oracle(rho, u, target_s=12.0, slab=8):
                                                 f"field, {steps} steps, FP64"}
 
 
+def oracle_full_field(rho, u, steps=2):
+    """The cpu_baseline leg: the FP64 oracle on a bounded sample of the
+    workload -- the whole benchmark field advanced `steps` steps -- timed on one
+    host core (initialisation excluded).  Its velocity is also the reference
+    that the GPU's runs of the same steps are compared with."""
+    import oracle
+    w = WORKLOAD
+    n = (w["nx"], w["ny"], w["nz"])
+    o = oracle.Oracle(3, n, lam=tuple(w["stretch"]), T=w["T"], nu=w["nu"])
+    o.init(rho, u)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    u_ref = o.macros()[1]
+    del o
+    cells = n[0] * n[1] * n[2]
+    info = {"cells": cells, "steps": steps, "seconds": round(dt, 3),
+            "sample": f"the whole {n[0]}x{n[1]}x{n[2]} benchmark field, {steps} steps, FP64, one core"}
+    return cells * steps / dt / 1e6, info, u_ref
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -241,41 +273,62 @@ def reference_arm(args):
     return 0
 
 
-def serve_arm(args):
-    """Served mix (the seeded trace of D3Q27 shear-wave and Taylor-Green solves):
-    continuous batching against one-at-a-time plain solves on the same GPU."""
-    import torch
-
-    from paper_2101_04550_gb300 import elbm, serve
-    elbm.load()
-    trace = serve.make_trace(args.serve_requests, rate=20.0, seed=0, steps=2000)
-    stream = torch.cuda.current_stream()
+def served_comparison(stream, n_requests, full=False):
+    """Served mix (the seeded trace of D3Q27 shear-wave and Taylor-Green
+    solves, Poisson arrivals at 20/s, 2000 steps each): continuous batching
+    against one-at-a-time plain service on the same GPU.  Every request's
+    final velocity in the batched run is compared with its plain run (the
+    same kernels, so bit for bit)."""
+    from paper_2101_04550_gb300 import serve
+    trace = serve.make_trace(n_requests, rate=20.0, seed=0, steps=2000)
     # warm-up: one small request in both modes (module loading, first graph capture)
     warm = serve.make_trace(4, rate=1000.0, seed=99, steps=20, sizes=(32, 48))
     for kernels in ("auto", "two-pass"):
         serve.Server(stream=stream, kernels=kernels).run(warm, mode="batched")
         serve.Server(stream=stream, kernels=kernels).run(warm, mode="plain")
     # "auto": the single-pass form for the grids it takes (x a multiple of 32, y of 16), two-pass for the rest
-    batched = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt").run(trace, mode="batched")
+    srv_srpt = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt")
+    batched = srv_srpt.run(trace, mode="batched")
     batched_fifo = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream).run(trace, mode="batched")
-    plain = serve.Server(stream=stream).run(trace, mode="plain")
-    batched_two_pass = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt",
-                                    kernels="two-pass").run(trace, mode="batched")
+    srv_plain = serve.Server(stream=stream)
+    plain = srv_plain.run(trace, mode="plain")
     plain_two_pass = serve.Server(stream=stream, kernels="two-pass").run(trace, mode="plain")
-    line = {"metric": "served aggregate MLUPS", "value": batched["aggregate_MLUPS"], "unit": "MLUPS",
+    same = [np.array_equal(srv_srpt.results[r.rid]["u"], srv_plain.results[r.rid]["u"])
+            for r in trace if r.rid in srv_srpt.results and r.rid in srv_plain.results]
+    out = {"workload": "served mix: Poisson arrivals 20/s of D3Q27 shear-wave and Taylor-Green solves, sizes "
+                       "{32,48,64,96,128}^3 and 64x32x64 (stretch 2 in y), T in [1/3, 0.6], advection 0-0.3, "
+                       "2000 steps each, FP32-shift and FP16-shift storage",
+           "requests": len(trace), "hbm_budget_GiB": 8, "chunk_steps": 100,
+           "batched_srpt": batched, "batched_fifo": batched_fifo, "plain": plain, "plain_two_pass": plain_two_pass,
+           "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 8 Mi nodes; "
+                     "fifo: arrival order, every resident solve each chunk",
+           "kernels": "single pass for grids with x % 32 == 0 and y % 16 == 0, two-pass batched kernels for the "
+                      "rest; plain_two_pass: one request at a time, two-pass for every solve",
+           # against the faster one-at-a-time service (alone, a small grid fills the GPU better in the
+           # two-pass form than in the single pass)
+           "speedup_vs_plain": batched["aggregate_MLUPS"] / max(plain["aggregate_MLUPS"],
+                                                                plain_two_pass["aggregate_MLUPS"]),
+           "accuracy": {"requests_compared": len(same), "batched_equals_plain_bitwise": bool(all(same)),
+                        "note": "each request's batched result against its plain (solo) result; the oracle "
+                                "comparison of served requests (1e-5 FP32, 2e-3 FP16) is a GPU test"}}
+    if full:
+        out["batched_two_pass"] = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt",
+                                               kernels="two-pass").run(trace, mode="batched")
+    return out
+
+
+def serve_arm(args):
+    """The served mix alone, with the batched two-pass form as well."""
+    import torch
+
+    from paper_2101_04550_gb300 import elbm
+    elbm.load()
+    sv = served_comparison(torch.cuda.current_stream(), args.serve_requests, full=True)
+    line = {"metric": "served aggregate MLUPS", "value": sv["batched_srpt"]["aggregate_MLUPS"], "unit": "MLUPS",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32 compute, f32/f16 shifted storage",
-            "data": "synthetic", "config": {"workload": "served mix: Poisson arrivals 20/s of D3Q27 shear-wave "
-                                                        "and Taylor-Green solves, 2000 steps each",
-                                            "requests": len(trace), "hbm_budget_GiB": 8, "chunk_steps": 100},
-            "batched": batched, "batched_fifo": batched_fifo, "plain": plain,
-            "batched_two_pass": batched_two_pass, "plain_two_pass": plain_two_pass,
-            "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 8 Mi nodes",
-            "kernels": "single pass for grids with x % 32 == 0 and y % 16 == 0 (one graph per solve, run side "
-                       "by side), two-pass batched kernels for the rest; *_two_pass: two-pass for every solve",
-            # against the faster one-at-a-time service (alone, a small grid fills the GPU better in the
-            # two-pass form than in the single pass)
-            "speedup_vs_plain": batched["aggregate_MLUPS"] / max(plain["aggregate_MLUPS"],
-                                                                 plain_two_pass["aggregate_MLUPS"])}
+            "data": "synthetic", "config": {"workload": sv["workload"], "requests": sv["requests"],
+                                            "hbm_budget_GiB": 8, "chunk_steps": 100},
+            "served": sv}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -287,11 +340,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
-    ap.add_argument("--kernel", type=int, default=3, choices=[0, 1, 2, 3],
-                    help="0 automatic, 1 two-pass in place, 2 graph-pipelined in place, 3 single pass (two arrays)")
+    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 automatic (the library's default: single pass where it applies), 1 two-pass in place, "
+                         "2 graph-pipelined in place, 3 single pass (two arrays)")
     ap.add_argument("--reduce-every", type=int, default=100)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (and with it the accuracy check that uses its result)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-mix comparison")
     ap.add_argument("--serve", action="store_true",
                     help="serve the seeded request mix (200 Poisson arrivals at 20/s) batched and plain instead")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -323,11 +379,16 @@ def main():
     s_bytes = elbm.STORAGE_BYTES[storage]
     Q = 27
     alg_bytes_per_cell = 2 * Q * s_bytes
+    full_size = args.nodes == 256
 
-    def timed_run(storage, kernel, steps, reduce_every, T=None):
+    def solver(storage, kernel, T=None):
+        return elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"],
+                           T=w["T"] if T is None else T, nu=w["nu"], storage=storage,
+                           stream=torch.cuda.current_stream(), kernel=kernel)
+
+    def timed_run(storage, kernel, steps, reduce_every):
         stream = torch.cuda.current_stream()
-        s = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"] if T is None else T,
-                        nu=w["nu"], storage=storage, stream=stream, kernel=kernel)
+        s = solver(storage, kernel)
         s.init(torch.as_tensor(rho, device="cuda"), torch.as_tensor(u, device="cuda"))
         s.step(args.warmup)
         s.reduce()
@@ -359,16 +420,24 @@ def main():
         launches = s.launches - launches0
         return s, total_s, step_s, launches, red
 
+    def two_steps(storage, kernel):
+        """Velocity after two steps from the benchmark field (the accuracy check)."""
+        with solver(storage, kernel) as s:
+            s.init(torch.as_tensor(rho, device="cuda"), torch.as_tensor(u, device="cuda"))
+            s.step(2)
+            return s.moments(dtype=np.float32)[1]
+
     # ---- main measurement ------------------------------------------------
     with ClockSampler(local) as clocks:
         s, total_s, step_s, launches, red = timed_run(storage, args.kernel, args.steps, args.reduce_every)
+    form = s.kernel_form[0]
     t_max = max_over_ranks(total_s, pg)
     value = aggregate_mlups(world, cells, args.steps, t_max)
     ms_per_step = t_max / args.steps * 1e3
     peak, peak_kind = hbm_peak()
     achieved = cells * args.steps * alg_bytes_per_cell / step_s / 1e9
     src_hash = kernel_source_hash()
-    traffic = MEASURED_TRAFFIC.get((src_hash, args.storage, args.kernel))
+    traffic = MEASURED_TRAFFIC.get((src_hash, args.storage, form)) if full_size else None
     mass_ok = red is not None and red["nonfinite"] == 0
 
     # ---- end to end through the public API with host buffers ------------
@@ -382,9 +451,7 @@ def main():
     s.close()
     del s
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    s2 = elbm.Solver(elbm.D3Q27, (w["nx"], w["ny"], w["nz"]), stretch=w["stretch"], T=w["T"],
-                     nu=w["nu"], storage=storage, stream=stream, kernel=args.kernel)
+    s2 = solver(storage, args.kernel)
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
@@ -405,21 +472,20 @@ def main():
 
     # ---- variants (same workload, other storage / kernel form) ----------
     variants = {}
+    var_steps = max(50, min(args.steps, 200))
+    D3_VARIANTS = (("f32_shift_two_pass", elbm.F32_SHIFT, 1), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2),
+                   ("f16_shift_single_pass", elbm.F16_SHIFT, 3), ("f16_shift_two_pass", elbm.F16_SHIFT, 1))
     if not args.no_variants and rank == 0:
-        for name, st, ker, T in (("f32_shift_two_pass", elbm.F32_SHIFT, 1, None),
-                                 ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2, None),
-                                 ("f16_shift_single_pass", elbm.F16_SHIFT, 3, None),
-                                 ("f16_shift_two_pass", elbm.F16_SHIFT, 1, None)):
-            sv, tot, sts, _, _ = timed_run(st, ker, min(args.steps, 200), args.reduce_every, T)
+        for name, st, ker in D3_VARIANTS:
+            sv, tot, sts, _, _ = timed_run(st, ker, var_steps, args.reduce_every)
             sv.close()
-            nsteps = min(args.steps, 200)
             b = 2 * Q * elbm.STORAGE_BYTES[st]
-            variants[name] = {"MLUPS": cells * nsteps / tot / 1e6,
-                              "step_MLUPS": cells * nsteps / sts / 1e6,
-                              "roofline_frac": cells * nsteps * b / sts / 1e9 / peak}
+            variants[name] = {"MLUPS": cells * var_steps / tot / 1e6,
+                              "step_MLUPS": cells * var_steps / sts / 1e6,
+                              "roofline_frac": cells * var_steps * b / sts / 1e9 / peak, "steps": var_steps}
 
-    # ---- the channel configuration: walls + body force (two-pass) -------
-    if not args.no_variants and rank == 0 and args.nodes == 256:
+    # ---- the channel configuration: walls + body force ------------------
+    if not args.no_variants and rank == 0 and full_size:
         from paper_2101_04550_gb300 import inputs
         c = CHANNEL
         nch = (c["nx"], c["ny"], c["nz"])
@@ -435,26 +501,83 @@ def main():
             sc.sync()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            nsteps = min(args.steps, 200)
             a.record(stream)
-            sc.step(nsteps)
+            sc.step(var_steps)
             b.record(stream)
             torch.cuda.synchronize()
-            red = sc.reduce()
+            red_c = sc.reduce()
             sc.close()
             sts = a.elapsed_time(b) / 1e3
             ncell = nch[0] * nch[1] * nch[2]
             bb = 2 * Q * elbm.STORAGE_BYTES[st]
-            variants[name] = {"MLUPS": ncell * nsteps / sts / 1e6, "step_MLUPS": ncell * nsteps / sts / 1e6,
-                              "roofline_frac": ncell * nsteps * bb / sts / 1e9 / peak,
-                              "workload": c["workload"], "finite": red["nonfinite"] == 0}
+            variants[name] = {"MLUPS": ncell * var_steps / sts / 1e6, "step_MLUPS": ncell * var_steps / sts / 1e6,
+                              "roofline_frac": ncell * var_steps * bb / sts / 1e9 / peak, "steps": var_steps,
+                              "workload": c["workload"], "finite": red_c["nonfinite"] == 0}
         del crho, cu
 
-    # ---- CPU baseline (oracle), rank 0 at N = 1 only ---------------------
+    # ---- D2Q9 double shear layer (Sec. III.C), cubic and stretched ------
+    if not args.no_variants and rank == 0 and full_size:
+        from paper_2101_04550_gb300 import inputs
+        stream = torch.cuda.current_stream()
+        U, Re, T2 = 0.2, 3e4, 0.5
+        for name, n2, lam2 in (("d2q9_dsl_1024x1024", (1024, 1024), (1.0, 1.0)),
+                               ("d2q9_dsl_1024x512_lam2", (1024, 512), (1.0, 2.0)),
+                               ("d2q9_dsl_4096x4096", (4096, 4096), (1.0, 1.0))):
+            r2, u2 = inputs.double_shear_layer(n2, U=U)
+            nu2 = U * 1024 / Re  # nu = U L / Re with L = 1024 (the physical box of all three)
+            if n2[0] == 4096:
+                nu2 = U * 4096 / Re
+            steps2 = 1000
+            s_2 = elbm.Solver(elbm.D2Q9, n2, stretch=lam2, T=T2, nu=nu2, storage=elbm.F32, stream=stream)
+            s_2.init(torch.as_tensor(r2, device="cuda"), torch.as_tensor(u2, device="cuda"))
+            s_2.step(args.warmup)
+            s_2.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s_2.step(steps2)
+            b.record(stream)
+            torch.cuda.synchronize()
+            red_2 = s_2.reduce(raise_nonfinite=False)
+            form2 = s_2.kernel_form[0]
+            s_2.close()
+            sts = a.elapsed_time(b) / 1e3
+            n_nodes = n2[0] * n2[1]
+            pop_bytes = 9 * n_nodes * 4
+            variants[name] = {"MLUPS": n_nodes * steps2 / sts / 1e6, "step_MLUPS": n_nodes * steps2 / sts / 1e6,
+                              "roofline_frac": n_nodes * steps2 * 72 / sts / 1e9 / peak, "steps": steps2,
+                              "alg_bytes_per_node": 72, "kernel": KERNEL_NAMES[form2],
+                              "workload": f"D2Q9 double shear layer {n2[0]}x{n2[1]}, stretch {lam2}, T = 0.5, "
+                                          f"U = 0.2, Re = 3e4, FP32",
+                              "l2_resident": pop_bytes < 129e6, "population_MB": pop_bytes / 1e6,
+                              "finite": red_2["nonfinite"] == 0}
+
+    # ---- served mix: batched against one request at a time --------------
+    served = None
+    if not args.no_serve and rank == 0 and world == 1 and full_size:
+        served = served_comparison(torch.cuda.current_stream(), args.serve_requests)
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only, and accuracy ------
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        mlups, info = time_oracle(rho, u, target_s=12.0, slab=8)
+        tol = {elbm.F32: 1e-5, elbm.F32_SHIFT: 1e-5, elbm.F16_SHIFT: 2e-3, elbm.BF16_SHIFT: 2e-2}
+        gpu_u = {"timed": two_steps(storage, args.kernel)}
+        if not args.no_variants:
+            for name, st, ker in D3_VARIANTS:
+                gpu_u[name] = two_steps(st, ker)
+        torch.cuda.synchronize()
+        mlups, info, u_ref = oracle_full_field(rho, u, steps=2)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": info["sample"]}
+        mean = u_ref.reshape(3, -1).mean(axis=1).reshape(3, 1, 1, 1)
+        per = {}
+        for name, ug in gpu_u.items():
+            ug = ug.astype(np.float64)
+            st = storage if name == "timed" else dict((n, st) for n, st, _ in D3_VARIANTS)[name]
+            per[name] = {"rel_linf_u": rel_linf(ug, u_ref), "rel_linf_u_minus_mean": rel_linf(ug - mean, u_ref - mean),
+                         "tolerance": tol[st]}
+        accuracy = {"reference": "FP64 oracle (the cpu_baseline run): the benchmark field, 2 steps, every node",
+                    "norm": "max|u_gpu - u_oracle| / max|u_oracle|", **per.pop("timed"), "variants": per}
 
     if rank == 0:
         line = {
@@ -463,7 +586,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["workload"], "lattice": "D3Q27", "nodes": [w["nx"], w["ny"], w["nz"]],
-                       "storage": args.storage, "kernel": KERNEL_NAMES[args.kernel],
+                       "storage": args.storage, "kernel": KERNEL_NAMES[form], "kernel_option": args.kernel,
                        "T": w["T"], "nu": w["nu"], "u_rms": w["u_rms"],
                        "reduce_every": args.reduce_every, "global_batch": world,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
@@ -471,10 +594,14 @@ def main():
                              % (cells * Q * s_bytes / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, "
+                                            "captured at 192^3 on these kernel sources and scaled to 256^3 by the "
+                                            "node count" if traffic else
+                                            "null: no ncu capture of these kernel sources and form"),
                          "peak_kind": peak_kind,
                          # context: the HBM3e data-sheet figure (the measured copy bandwidth is the denominator)
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                         "kernel": KERNEL_LAUNCHES[args.kernel],
+                         "kernel": KERNEL_LAUNCHES[form],
                          "alg_bytes_per_node": alg_bytes_per_cell,
                          "kernel_ms_per_step": step_s / args.steps * 1e3},
             "e2e": {"value": aggregate_mlups(world, cells, e2e_steps, e2e_s), "unit": "MLUPS",
@@ -482,7 +609,9 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "variants": variants,
+            "served": served,
             "diagnostics_finite": mass_ok,
             "kernel_source": src_hash,
         }

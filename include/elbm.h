@@ -277,10 +277,10 @@ int elbm_get_u_ref(const elbm_solver* s, double* out);
  * Allocation-free step.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory themselves -- applications
  * that route every device allocation through their own pool, plugins whose
- * host framework forbids allocations on its threads, or code that records
- * CUDA work where cudaMalloc is not allowed.  It creates no solver and calls
- * no allocating routine; the caller passes the populations and gets them back
- * advanced.
+ * host framework forbids allocations on its threads, or code running where
+ * cudaMalloc, which may synchronise the device, is not allowed.  It creates
+ * no solver and calls no allocating routine; the caller passes the
+ * populations and gets them back advanced.
  *   f        device pointer to float populations f[Q][nz][ny][nx] (unshifted,
  *            layout of elbm_get_populations), advanced in place by nsteps
  *            two-pass steps and left in that same layout.
@@ -294,8 +294,12 @@ int elbm_get_u_ref(const elbm_solver* s, double* out);
  * example on two streams) race and give wrong results; serialise them.  The
  * first call on a device looks up the array's device address (set-up that
  * must not happen inside a stream capture), so make one call, for example
- * with nsteps = 0, before capturing.  Errors: ELBM_ERR_ARG,
- * ELBM_ERR_UNREALIZABLE, ELBM_ERR_CUDA; elbm_last_error() has the message.
+ * with nsteps = 0, before capturing.  That address is valid for the life of
+ * the device's context: after a cudaDeviceReset do not call this entry point
+ * on that device again in the same process.  A CUDA error still pending from
+ * the caller's earlier work is reported as ELBM_ERR_CUDA and left in place;
+ * nothing is launched then.  Errors: ELBM_ERR_ARG, ELBM_ERR_UNREALIZABLE,
+ * ELBM_ERR_CUDA; elbm_last_error() has the message.
  */
 int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const double* stretch, double T,
                       double nu, float* f, int nsteps, void* stream);

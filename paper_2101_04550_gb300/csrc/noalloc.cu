@@ -3,13 +3,15 @@
 // For callers that cannot allocate device memory themselves: a host
 // application that manages all device memory through its own pool, a plugin
 // running inside a framework that forbids allocations on its worker threads,
-// or code recording CUDA work at a point where cudaMalloc is not allowed.
+// or code running at a point where cudaMalloc, which may synchronise the
+// device, is not allowed.
 // They pass their own population buffer; the only scratch the two-pass step
 // needs -- the anomaly field, three floats per node -- lives in a file-scope
 // device array of fixed size that every GPU loading this library holds until
 // the process exits.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <mutex>
 
 #include "step_kernels.cuh"
@@ -23,7 +25,10 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) float g_noalloc_q[3 * kNoallocMaxNodes];
 
 // Device address of g_noalloc_q, looked up once per device (the host-side
-// symbol is only a stand-in and must never be passed to a kernel).
+// symbol is only a stand-in and must never be passed to a kernel).  The
+// address lives as long as the device's primary context: after a
+// cudaDeviceReset it is stale, and this entry point must not be used on that
+// device again in the same process.
 float* g_q_addr[kMaxDevices] = {};
 std::mutex g_q_lock;
 
@@ -79,7 +84,16 @@ extern "C" int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const doub
     if (T >= lmin2) return noalloc_fail(ELBM_ERR_UNREALIZABLE, "T >= min lam^2: rest population not positive");
     if (!(nu > 0.0) || !std::isfinite(nu)) return noalloc_fail(ELBM_ERR_ARG, "nu must be finite and > 0");
 
-    (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
+    // An error still pending from the caller's earlier CUDA work is the
+    // caller's: report it and leave it in place rather than clear it, so that
+    // the error checks below see only this call's own launches.
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg, "a CUDA error from earlier work is pending (left in place): %s",
+                      cudaGetErrorString(pending));
+        return noalloc_fail(ELBM_ERR_CUDA, msg);
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return noalloc_fail(ELBM_ERR_CUDA, "no usable current device");
