@@ -290,25 +290,36 @@ def served_comparison(stream, n_requests, full=False):
     srv_srpt = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt")
     batched = srv_srpt.run(trace, mode="batched")
     batched_fifo = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream).run(trace, mode="batched")
+    # the same, with the single-pass batches as per-member graphs instead of the flattened launch
+    batched_graphs = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt",
+                                  sp_config=6).run(trace, mode="batched")
     srv_plain = serve.Server(stream=stream)
     plain = srv_plain.run(trace, mode="plain")
     plain_two_pass = serve.Server(stream=stream, kernels="two-pass").run(trace, mode="plain")
-    same = [np.array_equal(srv_srpt.results[r.rid]["u"], srv_plain.results[r.rid]["u"])
-            for r in trace if r.rid in srv_srpt.results and r.rid in srv_plain.results]
+    both = [r for r in trace if r.rid in srv_srpt.results and r.rid in srv_plain.results]
+    # NaN == NaN here: a solve that goes non-finite must do so identically in both runs
+    same = [np.array_equal(srv_srpt.results[r.rid]["u"], srv_plain.results[r.rid]["u"], equal_nan=True)
+            for r in both]
+    nonfinite = sum(1 for r in both if not np.isfinite(srv_plain.results[r.rid]["u"]).all())
     out = {"workload": "served mix: Poisson arrivals 20/s of D3Q27 shear-wave and Taylor-Green solves, sizes "
                        "{32,48,64,96,128}^3 and 64x32x64 (stretch 2 in y), T in [1/3, 0.6], advection 0-0.3, "
                        "2000 steps each, FP32-shift and FP16-shift storage",
            "requests": len(trace), "hbm_budget_GiB": 8, "chunk_steps": 100,
-           "batched_srpt": batched, "batched_fifo": batched_fifo, "plain": plain, "plain_two_pass": plain_two_pass,
+           "batched_srpt": batched, "batched_fifo": batched_fifo, "batched_srpt_member_graphs": batched_graphs,
+           "plain": plain, "plain_two_pass": plain_two_pass,
            "policy": "srpt: admit the smallest waiting solve; step the least remaining work up to 8 Mi nodes; "
                      "fifo: arrival order, every resident solve each chunk",
-           "kernels": "single pass for grids with x % 32 == 0 and y % 16 == 0, two-pass batched kernels for the "
-                      "rest; plain_two_pass: one request at a time, two-pass for every solve",
+           "kernels": "single pass for grids with x % 32 == 0 and y % 16 == 0 (one flattened launch per step "
+                      "over those solves, configuration from the library's autotuner), two-pass batched kernels "
+                      "for the rest; batched_srpt_member_graphs: the single-pass solves as per-member graphs; "
+                      "plain_two_pass: one request at a time, two-pass for every solve",
            # against the faster one-at-a-time service (alone, a small grid fills the GPU better in the
            # two-pass form than in the single pass)
            "speedup_vs_plain": batched["aggregate_MLUPS"] / max(plain["aggregate_MLUPS"],
                                                                 plain_two_pass["aggregate_MLUPS"]),
            "accuracy": {"requests_compared": len(same), "batched_equals_plain_bitwise": bool(all(same)),
+                        "requests_differing": int(len(same) - sum(same)),
+                        "requests_nonfinite": nonfinite,
                         "note": "each request's batched result against its plain (solo) result; the oracle "
                                 "comparison of served requests (1e-5 FP32, 2e-3 FP16) is a GPU test"}}
     if full:
@@ -333,6 +344,45 @@ def serve_arm(args):
     return 0
 
 
+def d2q9_arm(args):
+    """The D2Q9 double shear layer (Sec. III.C) on an N x N grid alone: U = 0.2,
+    Re = 3e4 (nu = U N / Re), T = 0.5, FP32 storage, the automatic kernel form."""
+    import torch
+
+    from paper_2101_04550_gb300 import elbm, inputs
+    elbm.load()
+    n = (args.d2q9, args.d2q9)
+    rho, u = inputs.double_shear_layer(n, U=0.2)
+    stream = torch.cuda.current_stream()
+    with elbm.Solver(elbm.D2Q9, n, T=0.5, nu=0.2 * n[0] / 3e4, storage=elbm.F32, stream=stream,
+                     kernel=args.kernel) as s:
+        s.init(torch.as_tensor(rho, device="cuda"), torch.as_tensor(u, device="cuda"))
+        s.step(args.warmup)
+        s.sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        l0 = s.launches
+        a.record(stream)
+        s.step(args.steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        form, variant = s.kernel_form
+        launches = s.launches - l0
+    sec = a.elapsed_time(b) / 1e3
+    peak, peak_kind = hbm_peak()
+    mlups = n[0] * n[1] * args.steps / sec / 1e6
+    line = {"metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"D2Q9 double shear layer {n[0]}x{n[1]}", "kernel": KERNEL_NAMES[form],
+                       "variant": variant},
+            "roofline": {"bound": "hbm", "achieved": mlups * 72 / 1e3, "peak": peak, "unit": "GB/s",
+                         "frac": mlups * 72 / 1e3 / peak, "peak_kind": peak_kind, "alg_bytes_per_node": 72},
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,6 +403,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--nodes", type=int, default=256,
                     help="edge of the cubic grid (256 = the benchmark workload; smaller only for profiling)")
+    ap.add_argument("--d2q9", type=int, default=0,
+                    help="time only the D2Q9 double shear layer on an N x N grid (automatic form) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -361,6 +413,8 @@ def main():
         return reference_arm(args)
     if args.serve:
         return serve_arm(args)
+    if args.d2q9:
+        return d2q9_arm(args)
 
     import torch
 

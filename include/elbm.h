@@ -73,25 +73,27 @@ extern "C" {
 #define ELBM_OPT_EQUILIBRIUM 1
 /* ELBM_OPT_KERNEL: the form of the step; every form evaluates the same per-node
  *   arithmetic and gives bit-identical results.
- *   0 = automatic (the default): the single pass (form 3, TMEM kernel) on
- *       D3Q27 grids with nx a multiple of 32 and ny of 16, for which
- *       elbm_create (or setting this option) then allocates the second
- *       population array -- twice the population memory; if that allocation
- *       fails the solver keeps one array and steps in the two-pass form.
- *       Every other grid, D2Q9, and the second-order equilibrium: the
- *       two-pass form.  elbm_kernel_form() reports the choice;
+ *   0 = automatic (the default): the single pass (form 3) on D3Q27 grids
+ *       with nx a multiple of 32 and ny of 16 (TMEM kernel) and on periodic,
+ *       unforced D2Q9 grids, for which elbm_create (or setting this option)
+ *       allocates the second population array -- twice the population
+ *       memory; if that allocation fails the solver keeps one array and steps
+ *       in the two-pass form.  Other D3Q27 grids, D2Q9 with walls or a force,
+ *       and the second-order equilibrium: the two-pass form.
+ *       elbm_kernel_form() reports the choice;
  *   1 = two-pass, in place: an anomaly pass over the grid, then the collide pass;
  *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide
  *       kernels, so that the collide kernels re-read populations from L2;
  *       forms 1 and 2 release a second population array if one is held;
- *   3 = single pass with a second population array (D3Q27 only): every block
- *       recomputes the anomaly around its tile and reads the populations once
- *       (TMA-fed, populations parked in tensor memory, when nx is a multiple
- *       of 32 and ny of 16; 32 x 8 TMA tiles when ny is a multiple of 8;
- *       cp.async-staged otherwise).  Setting it allocates the second array.
+ *   3 = single pass with a second population array: every block recomputes
+ *       the anomaly around its tile and reads the populations once.  D3Q27:
+ *       TMA-fed with the populations parked in tensor memory when nx is a
+ *       multiple of 32 and ny of 16; 32 x 8 TMA tiles when ny is a multiple
+ *       of 8; cp.async-staged otherwise.  D2Q9: strips of 126 columns
+ *       marching along y, any grid.  Setting it allocates the second array.
  *   The second-order equilibrium always runs in the two-pass form; walls and
- *   the body force run in form 3 only on its TMEM geometry (nx a multiple of
- *   32, ny of 16) and in the two-pass form otherwise. */
+ *   the body force run in form 3 only on the D3Q27 TMEM geometry (nx a
+ *   multiple of 32, ny of 16) and in the two-pass form otherwise. */
 #define ELBM_OPT_KERNEL      2
 /* ELBM_OPT_RHO_REF: reference density of the shifted storage (before init). */
 #define ELBM_OPT_RHO_REF     3
@@ -207,7 +209,8 @@ int elbm_sync(elbm_solver* s);
  * 3 single pass (ELBM_OPT_KERNEL and the grid decide it; see there), or
  * ELBM_ERR_ARG for NULL.  For form 3, *variant (if not NULL) receives the
  * single-pass kernel: 1 TMEM (32 x 16 tiles), 2 TMA (32 x 8 tiles),
- * 3 cp.async-staged; 0 for the other forms.  Host-side query, no CUDA call. */
+ * 3 cp.async-staged (D3Q27), 4 the D2Q9 row march; 0 for the other forms.
+ * Host-side query, no CUDA call. */
 int elbm_kernel_form(const elbm_solver* s, int* variant);
 
 /* Informational queries. */
@@ -234,11 +237,21 @@ long long elbm_launch_count(const elbm_solver* s);
  *    refreshed at every elbm_batch_step.  One live batch of this form per
  *    (lattice, storage mode) and device may exist at a time;
  *    elbm_batch_create returns ELBM_ERR_STATE for a second one;
- *  - single-pass members (ELBM_OPT_KERNEL 3, D3Q27, two population arrays;
- *    walls and body force allowed where the single pass takes them): each
- *    member's sequence of nsteps single-pass steps is captured once as a CUDA
- *    graph and replayed on private streams of the batch, so the members run
- *    side by side.
+ *  - single-pass members (kernel form 3, D3Q27, two population arrays;
+ *    walls and body force allowed where the single pass takes them): the
+ *    members on the TMEM geometry (nx a multiple of 32, ny of 16) advance in
+ *    one launch per step of a flattened kernel over a work list of (member,
+ *    32 x 16 tile column, z segment) items, with every member's parameter block
+ *    and tensor maps in device memory of the batch; the nsteps launches are
+ *    captured as a CUDA graph and replayed.  The segment depth (32, 16 or 8
+ *    planes) and the order of the work list come from an autotuner (see
+ *    elbm_batch_tuning), which may also choose per-member graphs: each
+ *    member's sequence of solo single-pass launches captured once and replayed
+ *    on private streams of the batch, side by side -- the form other
+ *    single-pass members (32 x 8 TMA or cp.async kernels) always take.  If any
+ *    member has walls or a body force, the flattened launch uses the kernel
+ *    that honours them for every member (same bits for the others).  Any
+ *    number of single-pass batches may be live at once.
  * Mixing the forms in one batch returns ELBM_ERR_ARG.
  */
 typedef struct elbm_batch elbm_batch;
@@ -267,6 +280,30 @@ int elbm_batch_step(elbm_batch* b, int nsteps);
  * tuning step times in ms (128, 256) and the number of kernel launches issued
  * so far. */
 int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long long* launches);
+
+/* Single-pass form: the configuration the last elbm_batch_step used for the
+ * members the TMEM single pass takes, and the autotuner's timings of two
+ * steps of each candidate for the batch's size class (shared by every batch
+ * of the process with the same storage mode, walls/force setting and
+ * floor(log2(nodes)) of those members):
+ *   *config       0..5 the flattened launch (one kernel per step over a work
+ *                 list of tile columns of every such member), 6 per-member graphs;
+ *   *seg_planes   z planes per work item (32, 16 or 8; 0 for config 6);
+ *   *interleaved  1 if the work list interleaves the members item by item,
+ *                 0 if it takes them one after another;
+ *   ms[7]         tuning times in ms of configs 0..6 (-1 for one not yet timed).
+ * Any output pointer may be NULL.  Returns ELBM_OK once the tuning of the
+ * size class is complete, 1 while it is still in progress (the tuning spreads
+ * over calls with fewer than 14 steps; until it completes config 0 runs),
+ * ELBM_ERR_STATE for a two-pass batch or before the first single-pass step. */
+int elbm_batch_tuning(const elbm_batch* b, int* config, int* seg_planes, int* interleaved, double* ms);
+
+/* Single-pass form: run configuration `config` (0..6, as elbm_batch_tuning
+ * numbers them) from the next elbm_batch_step on instead of the autotuner's
+ * choice; -1 returns to the autotuner.  Every configuration computes the same
+ * bits.  ELBM_ERR_ARG for a value out of range, ELBM_ERR_STATE for a
+ * two-pass batch. */
+int elbm_batch_set_config(elbm_batch* b, int config);
 
 void elbm_batch_destroy(elbm_batch* b);
 

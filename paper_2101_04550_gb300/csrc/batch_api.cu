@@ -9,11 +9,20 @@
 //    one live batch of this form per kind and device.  A launch sequence of n
 //    steps is captured once as a CUDA graph; when membership changes the block
 //    total, the graph is re-captured and the executable graph updated in place.
-//  * Single-pass members (form 3, two population arrays each): every member's
-//    n-step sequence of single-pass launches is captured once as a graph of
-//    its own and replayed on a pool of private streams, so the members' blocks
-//    run side by side; a member's result is bit-identical to stepping it alone
-//    because it is the same sequence of launches.
+//  * Single-pass members (form 3, two population arrays each).  Members whose
+//    grids the TMEM single pass takes advance together in one launch per step
+//    of the flattened batch kernel (batch_single.cuh) over a work list of
+//    (member, tile column, z range) items; the n launches of a call are
+//    captured once as a CUDA graph and replayed.  The work list's segment
+//    depth and order come from an autotuner written here, which times two
+//    real steps of every candidate -- segments of 32, 16 or 8 planes, members
+//    one after another or interleaved, and per-member graphs -- and keeps the
+//    fastest per (storage, walls/force, size class of the batch) for the
+//    process.  Other single-pass members (32 x 8 TMA or cp.async kernels), and
+//    every member when the tuner picks it, run as per-member graphs: each
+//    member's n-step sequence of solo launches captured once and replayed on
+//    a pool of private streams, so the members' blocks run side by side.
+//    Either way a member's result is bit-identical to stepping it alone.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -58,6 +67,39 @@ struct elbm_batch {
     std::vector<Retired> retired;
     std::vector<cudaStream_t> pool;    // form 3: private streams the member graphs run on
     std::vector<cudaEvent_t> pool_done;
+    // form 3, flattened launch: member records (host copy and device table),
+    // the work list on the device and the graphs of n launches
+    struct SpCached {                  // a member's record, arrays in the order first seen
+        long long uid = 0;
+        const void* a0 = nullptr;
+        const void* a1 = nullptr;
+        std::vector<unsigned char> rec;
+    };
+    std::vector<SpCached> sp_cache;
+    std::vector<unsigned char> sp_table;
+    void* sp_table_dev = nullptr;
+    size_t sp_table_cap = 0;
+    void* sp_work_dev = nullptr;
+    size_t sp_work_cap = 0;
+    int sp_nwork = 0;
+    std::vector<long long> sp_work_sig;   // what the uploaded work list was built from
+    struct SpGraph {
+        cudaGraphExec_t exec = nullptr;
+        int nwork = 0;
+        bool bc = false;
+        bool fx = false;
+    };
+    std::map<int, SpGraph> sp_graphs;  // by step count
+    struct Staging {                   // pinned host buffer of an asynchronous upload
+        void* host = nullptr;
+        size_t cap = 0;
+        cudaEvent_t done = nullptr;    // recorded after the copy out of it
+    };
+    Staging sp_stage[2][2];            // [table, work list][alternate buffers]
+    int sp_stage_next[2] = {0, 0};
+    int sp_pinned = -1;                // configuration set by elbm_batch_set_config (-1: the autotuner's)
+    int sp_config = -1;                // configuration of the last flattened call
+    long long sp_key = -1;             // its tuning key
 };
 
 namespace {
@@ -90,6 +132,26 @@ constexpr int kPoolStreams = 16;     // private streams of a single-pass batch
 constexpr int kGraphsPerMember = 4;  // cached step counts per member
 
 int member_form(const elbm_solver* s) { return elbm::effective_kernel(s) == 3 ? 3 : 1; }
+
+// Autotuner candidates of the single-pass batch: configurations 0..5 are the
+// flattened launch with segments of kSegCand[c % 3] planes, members one after
+// another (c < 3) or interleaved item by item (c >= 3); configuration 6 is
+// per-member graphs.
+constexpr int kSpCandidates = 7;
+constexpr int kSpGraphs = 6;
+constexpr int kSegCand[3] = {32, 16, 8};
+struct SpTuning {
+    double ms[kSpCandidates] = {};
+    int next = 0;        // next candidate to time
+    int chosen = -1;
+};
+// Shared by every batch of the process, by (storage, walls/force, size class).
+std::map<long long, SpTuning> g_sp_tuning;
+
+bool bounded_member(const elbm_solver* s)
+{
+    return s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
+}
 
 // Hand the cached graphs of solver uid over for destruction once the work
 // enqueued so far on the batch's stream (which every member launch joins) is done.
@@ -161,7 +223,8 @@ cudaError_t member_graph(elbm_batch* b, elbm_solver* s, int nsteps, cudaStream_t
     if (e != cudaSuccess) return e;
     cudaError_t e1 = cudaSuccess;
     for (int k = 0; k < nsteps && e1 == cudaSuccess; ++k) {
-        e1 = elbm::step_single_impl<3>(seq, seq.f2, &g.launches);
+        e1 = (seq.D == 2) ? elbm::step_single_impl<2>(seq, seq.f2, &g.launches)
+                          : elbm::step_single_impl<3>(seq, seq.f2, &g.launches);
         std::swap(seq.f, seq.f2);
     }
     e = cudaStreamEndCapture(ps, &graph);
@@ -192,20 +255,18 @@ cudaError_t ensure_pool(elbm_batch* b, int n)
     return cudaSuccess;
 }
 
-// nsteps single-pass steps of every member: fork the pool streams from the
-// batch's stream, launch each member's graph on one of them, join them back.
-int step_single_form(elbm_batch* b, int nsteps)
+// nsteps single-pass steps of the given members as per-member graphs: fork
+// the pool streams from the batch's stream, launch each member's graph on one
+// of them, join them back.  The members' arrays are not swapped here.
+cudaError_t run_member_graphs(elbm_batch* b, const std::vector<elbm_solver*>& ms, int nsteps)
 {
-    for (const auto* s : b->members)
-        if (member_form(s) != 3 || s->parity != 0 || !s->f2)
-            return bfail(ELBM_ERR_STATE, "a member of a single-pass batch no longer steps in the single-pass form");
-    reap(b, false);
-    const int n = (int)b->members.size(), P = std::min(n, kPoolStreams);
+    if (ms.empty() || nsteps == 0) return cudaSuccess;
+    const int n = (int)ms.size(), P = std::min(n, kPoolStreams);
     cudaError_t e = ensure_pool(b, P);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_in, b->stream);
     for (int k = 0; k < P && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->pool[k], b->ev_in, 0);
     for (int k = 0; k < n && e == cudaSuccess; ++k) {
-        elbm_solver* s = b->members[k];
+        elbm_solver* s = ms[k];
         cudaGraphExec_t exec = nullptr;
         long long launches = 0;
         e = member_graph(b, s, nsteps, b->pool[k % P], &exec, &launches);
@@ -219,6 +280,273 @@ int step_single_form(elbm_batch* b, int nsteps)
         e = cudaEventRecord(b->pool_done[k], b->pool[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->pool_done[k], 0);
     }
+    return e;
+}
+
+cudaError_t join_in(elbm_batch* b);
+cudaError_t join_out(elbm_batch* b);
+
+// Size class of a set of flattened members: floor(log2(total nodes)).
+long long sp_key(const elbm_batch* b, const std::vector<elbm_solver*>& flat)
+{
+    long long nodes = 0;
+    bool bc = false;
+    for (const auto* s : flat) {
+        nodes += s->N;
+        bc = bc || bounded_member(s);
+    }
+    int cls = 0;
+    while ((2ll << cls) <= nodes) ++cls;
+    return ((long long)b->storage * 2 + (bc ? 1 : 0)) * 64 + cls;
+}
+
+// Enqueue the copy of `bytes` from src to dev on the batch's private stream
+// through pinned staging buffer pair `which` (0 table, 1 work list), so that
+// the copy does not make the host wait for the stream; a buffer is reused
+// once the copy out of it two uploads ago has run.
+cudaError_t staged_upload(elbm_batch* b, int which, void* dev, const void* src, size_t bytes)
+{
+    elbm_batch::Staging& st = b->sp_stage[which][b->sp_stage_next[which]];
+    b->sp_stage_next[which] ^= 1;
+    cudaError_t e = cudaSuccess;
+    if (st.done) e = cudaEventSynchronize(st.done);
+    if (e == cudaSuccess && bytes > st.cap) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.cap = 0;
+        e = cudaHostAlloc(&st.host, 2 * bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) st.cap = 2 * bytes;
+    }
+    if (e == cudaSuccess && !st.done) e = cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    std::memcpy(st.host, src, bytes);
+    e = cudaMemcpyAsync(dev, st.host, bytes, cudaMemcpyHostToDevice, b->exec_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(st.done, b->exec_stream);
+    return e;
+}
+
+// Member records of the flattened members into the device table, each with
+// the phase of its current array.
+cudaError_t sp_upload_table(elbm_batch* b, const std::vector<elbm_solver*>& flat)
+{
+    const size_t rb = elbm::sp_member_bytes();
+    b->sp_table.resize(rb * flat.size());
+    for (size_t k = 0; k < flat.size(); ++k) {
+        elbm_solver* s = flat[k];
+        elbm_batch::SpCached* c = nullptr;
+        for (auto& x : b->sp_cache)
+            if (x.uid == s->uid) c = &x;
+        const bool same = c && ((c->a0 == s->f && c->a1 == s->f2) || (c->a0 == s->f2 && c->a1 == s->f));
+        if (!c) {
+            b->sp_cache.push_back({});
+            c = &b->sp_cache.back();
+        }
+        elbm::Solver fixed = *s;  // arrays in the record's order
+        if (same) {
+            fixed.f = const_cast<void*>(c->a0);
+            fixed.f2 = const_cast<void*>(c->a1);
+        } else {
+            c->uid = s->uid;
+            c->a0 = s->f;
+            c->a1 = s->f2;
+            c->rec.assign(rb, 0);
+        }
+        const cudaError_t e = elbm::sp_member_fill(fixed, c->rec.data(), !same);
+        if (e != cudaSuccess) return e;
+        unsigned char* rec = b->sp_table.data() + k * rb;
+        std::memcpy(rec, c->rec.data(), rb);
+        elbm::sp_member_set_phase(rec, s->f == c->a0 ? 0 : 1);
+    }
+    const size_t bytes = b->sp_table.size();
+    if (bytes > b->sp_table_cap) {
+        cudaError_t e = cudaStreamSynchronize(b->exec_stream);  // nothing may still read the old table
+        if (b->sp_table_dev) cudaFree(b->sp_table_dev);
+        b->sp_table_dev = nullptr;
+        b->sp_table_cap = 0;
+        for (auto& kv : b->sp_graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        b->sp_graphs.clear();
+        if (e == cudaSuccess) e = cudaMalloc(&b->sp_table_dev, 2 * bytes);
+        if (e != cudaSuccess) return e;
+        b->sp_table_cap = 2 * bytes;
+    }
+    return staged_upload(b, 0, b->sp_table_dev, b->sp_table.data(), bytes);
+}
+
+// Work list of configuration c over the flattened members (rebuilt and
+// uploaded only when the members or the configuration change).
+cudaError_t sp_upload_work(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c)
+{
+    std::vector<long long> sig{c};
+    for (const auto* s : flat) sig.insert(sig.end(), {s->uid, s->nx, s->ny, s->nz});
+    if (sig == b->sp_work_sig && b->sp_work_dev) return cudaSuccess;
+    const int seg = kSegCand[c % 3];
+    std::vector<std::vector<int4>> per(flat.size());
+    for (size_t m = 0; m < flat.size(); ++m) {
+        const elbm_solver* s = flat[m];
+        for (int z0 = 0; z0 < s->nz; z0 += seg)
+            for (int y0 = 0; y0 < s->ny; y0 += 16)
+                for (int x0 = 0; x0 < s->nx; x0 += 32)
+                    per[m].push_back(make_int4((int)m, x0, y0, z0 | (std::min(s->nz, z0 + seg) << 16)));
+    }
+    std::vector<int4> work;
+    if (c < 3) {
+        for (auto& v : per) work.insert(work.end(), v.begin(), v.end());
+    } else {
+        for (size_t k = 0;; ++k) {
+            bool any = false;
+            for (auto& v : per)
+                if (k < v.size()) {
+                    work.push_back(v[k]);
+                    any = true;
+                }
+            if (!any) break;
+        }
+    }
+    const size_t bytes = work.size() * sizeof(int4);
+    if (bytes > b->sp_work_cap) {
+        cudaError_t e = cudaStreamSynchronize(b->exec_stream);
+        if (b->sp_work_dev) cudaFree(b->sp_work_dev);
+        b->sp_work_dev = nullptr;
+        b->sp_work_cap = 0;
+        for (auto& kv : b->sp_graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        b->sp_graphs.clear();
+        if (e == cudaSuccess) e = cudaMalloc(&b->sp_work_dev, 2 * bytes);
+        if (e != cudaSuccess) return e;
+        b->sp_work_cap = 2 * bytes;
+    }
+    b->sp_nwork = (int)work.size();
+    b->sp_work_sig = sig;
+    return staged_upload(b, 1, b->sp_work_dev, work.data(), bytes);
+}
+
+// nsteps steps of the flattened members in configuration c (0..5), as one
+// CUDA graph of nsteps launches (graph = true) or as direct launches.
+cudaError_t run_flat(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c, int nsteps, bool graph)
+{
+    bool bc = false, fx = true;
+    for (const auto* s : flat) {
+        bc = bc || bounded_member(s);
+        fx = fx && s->g[1] == 0.0 && s->g[2] == 0.0;
+    }
+    cudaError_t e = join_in(b);
+    if (e == cudaSuccess) e = sp_upload_table(b, flat);
+    if (e == cudaSuccess) e = sp_upload_work(b, flat, c);
+    if (e != cudaSuccess) return e;
+    if (!graph) {
+        e = elbm::sp_batch_enqueue(b->storage, bc, fx, b->sp_table_dev, b->sp_work_dev, b->sp_nwork, nsteps,
+                                   b->exec_stream, &b->launches);
+    } else {
+        elbm_batch::SpGraph& g = b->sp_graphs[nsteps];
+        if (!g.exec || g.nwork != b->sp_nwork || g.bc != bc || g.fx != fx) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            cudaGraph_t graph_ = nullptr;
+            long long dummy = 0;
+            e = cudaStreamBeginCapture(b->exec_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = elbm::sp_batch_enqueue(b->storage, bc, fx, b->sp_table_dev, b->sp_work_dev,
+                                                              b->sp_nwork, nsteps, b->exec_stream, &dummy);
+                e = cudaStreamEndCapture(b->exec_stream, &graph_);
+                if (e == cudaSuccess) e = e1;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph_, 0);
+            if (graph_) cudaGraphDestroy(graph_);
+            if (e != cudaSuccess) return e;
+            g.nwork = b->sp_nwork;
+            g.bc = bc;
+            g.fx = fx;
+        }
+        e = cudaGraphLaunch(g.exec, b->exec_stream);
+        if (e == cudaSuccess) b->launches += nsteps;
+    }
+    for (auto* s : flat) s->launches += nsteps;
+    if (e == cudaSuccess) e = join_out(b);
+    return e;
+}
+
+// Time two real steps of every candidate not yet timed for this size class
+// (as many as *steps_left allows); once all are timed the fastest is chosen.
+cudaError_t sp_tune(elbm_batch* b, const std::vector<elbm_solver*>& flat, SpTuning& t, int* steps_left)
+{
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    while (e == cudaSuccess && t.next < kSpCandidates && *steps_left >= 2) {
+        const int c = t.next;
+        // host-side preparation outside the timed interval: the uploads of a
+        // flattened configuration, the captures of the member graphs
+        if (c < kSpGraphs) {
+            e = join_in(b);
+            if (e == cudaSuccess) e = sp_upload_table(b, flat);
+            if (e == cudaSuccess) e = sp_upload_work(b, flat, c);
+            if (e == cudaSuccess) e = join_out(b);
+        } else {
+            e = ensure_pool(b, std::min((int)flat.size(), kPoolStreams));
+            for (size_t k = 0; k < flat.size() && e == cudaSuccess; ++k) {
+                cudaGraphExec_t exec = nullptr;
+                long long launches = 0;
+                e = member_graph(b, flat[k], 2, b->pool[k % b->pool.size()], &exec, &launches);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess) e = c < kSpGraphs ? run_flat(b, flat, c, 2, false) : run_member_graphs(b, flat, 2);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) break;
+        t.ms[c] = ms;
+        ++t.next;
+        *steps_left -= 2;  // two steps: every member's state is back in the array it started in
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (e == cudaSuccess && t.next == kSpCandidates && t.chosen < 0) {
+        t.chosen = 0;
+        for (int c = 1; c < kSpCandidates; ++c)
+            if (t.ms[c] < t.ms[t.chosen]) t.chosen = c;
+    }
+    return e;
+}
+
+// nsteps single-pass steps of every member.
+int step_single_form(elbm_batch* b, int nsteps)
+{
+    for (const auto* s : b->members)
+        if (member_form(s) != 3 || s->parity != 0 || !s->f2)
+            return bfail(ELBM_ERR_STATE, "a member of a single-pass batch no longer steps in the single-pass form");
+    reap(b, false);
+    std::vector<elbm_solver*> flat, graphed;
+    for (auto* s : b->members) (elbm::single_pass_variant(*s) == 1 ? flat : graphed).push_back(s);
+    cudaError_t e = cudaSuccess;
+    if (!flat.empty()) {
+        const long long key = sp_key(b, flat);
+        SpTuning* t = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_lock);
+            t = &g_sp_tuning[key];  // map nodes stay where they are
+        }
+        int left = nsteps;
+        // the tuning steps are real steps of the flattened members (an even
+        // number, so each state ends in the array it started in)
+        if (t->chosen < 0 && b->sp_pinned < 0) e = sp_tune(b, flat, *t, &left);
+        // while still tuning: 32-plane segments, member-major
+        const int c = b->sp_pinned >= 0 ? b->sp_pinned : t->chosen >= 0 ? t->chosen : 0;
+        b->sp_key = key;
+        b->sp_config = c;
+        if (e == cudaSuccess && left > 0) {
+            if (c < kSpGraphs) {
+                e = run_flat(b, flat, c, left, true);
+            } else if (left == nsteps) {
+                graphed.insert(graphed.end(), flat.begin(), flat.end());
+            } else {
+                e = run_member_graphs(b, flat, left);
+            }
+        }
+    }
+    if (e == cudaSuccess) e = run_member_graphs(b, graphed, nsteps);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return bcuda(e, "elbm_batch_step");
@@ -474,6 +802,34 @@ int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long
     return ELBM_OK;
 }
 
+int elbm_batch_set_config(elbm_batch* b, int config)
+{
+    if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
+    if (config < -1 || config >= kSpCandidates) return bfail(ELBM_ERR_ARG, "config must be -1 or 0..6");
+    if (b->form != 3) return bfail(ELBM_ERR_STATE, "only single-pass batches have a configuration");
+    b->sp_pinned = config;
+    return ELBM_OK;
+}
+
+int elbm_batch_tuning(const elbm_batch* b, int* config, int* seg_planes, int* interleaved, double* ms)
+{
+    if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
+    if (b->form != 3 || b->sp_key < 0) return bfail(ELBM_ERR_STATE, "no single-pass batch step has run");
+    SpTuning t;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        auto it = g_sp_tuning.find(b->sp_key);
+        if (it != g_sp_tuning.end()) t = it->second;
+    }
+    const int c = b->sp_config;
+    if (config) *config = c;
+    if (seg_planes) *seg_planes = c < kSpGraphs ? kSegCand[c % 3] : 0;
+    if (interleaved) *interleaved = c < kSpGraphs ? (c >= 3 ? 1 : 0) : 0;
+    if (ms)
+        for (int k = 0; k < kSpCandidates; ++k) ms[k] = k < t.next ? t.ms[k] : -1.0;
+    return t.chosen >= 0 ? ELBM_OK : 1;
+}
+
 void elbm_batch_destroy(elbm_batch* b)
 {
     if (!b) return;
@@ -483,6 +839,17 @@ void elbm_batch_destroy(elbm_batch* b)
     for (auto& g : b->member_graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     b->member_graphs.clear();
+    for (auto& kv : b->sp_graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    b->sp_graphs.clear();
+    if (b->sp_table_dev) cudaFree(b->sp_table_dev);
+    if (b->sp_work_dev) cudaFree(b->sp_work_dev);
+    for (auto& pair : b->sp_stage)
+        for (auto& st : pair) {
+            if (st.done) cudaEventSynchronize(st.done);
+            if (st.host) cudaFreeHost(st.host);
+            if (st.done) cudaEventDestroy(st.done);
+        }
     reap(b, true);
     for (size_t k = 0; k < b->pool.size(); ++k) {
         cudaEventDestroy(b->pool_done[k]);

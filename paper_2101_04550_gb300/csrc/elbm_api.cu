@@ -68,7 +68,11 @@ static bool shifted_storage(int storage) { return storage != ELBM_F32; }
 
 // Round-up multiplier and shift for floor(n / d), 0 <= n < 2^31, d >= 1:
 // t = umulhi(n, m), q = (t + n) >> s with s = ceil(log2 d) and
-// m = floor(2^32 (2^s - d) / d) + 1.
+// m = floor(2^32 (2^s - d) / d) + 1.  This is the unsigned division by an
+// invariant integer of Granlund and Montgomery ("Division by invariant
+// integers using multiplication", PLDI 1994, Sec. 4): the 33-bit multiplier
+// 2^32 + m; for n < 2^31 the sum t + n cannot overflow 32 bits, so the
+// shift needs no halving step.
 static void host_divider(unsigned d, unsigned* m, int* s)
 {
     int k = 0;
@@ -127,17 +131,29 @@ void fill_params(const Solver& s, StepParams& p)
     p.parity = s.parity;
 }
 
-// Kernel form a step uses.  Automatic (0): the TMEM single pass on the D3Q27
-// grids it takes (x a multiple of 32 nodes, y of 16) once its second
-// population array has been allocated, the two-pass form otherwise.  The
-// second-order equilibrium runs in the two-pass form; walls and the body force
-// in the two-pass form or, where its geometry allows, the TMEM single pass.
+// Kernel form a step uses.  Automatic (0): once the second population array
+// has been allocated, the single pass on the D3Q27 grids its TMEM kernel takes
+// (x a multiple of 32 nodes, y of 16) and on periodic, unforced D2Q9 grids;
+// the two-pass form otherwise.  The second-order equilibrium runs in the
+// two-pass form; walls and the body force in the two-pass form or, on the
+// TMEM geometry of D3Q27, the TMEM single pass (the D2Q9 single pass has
+// neither).
+static bool bounded_solver(const Solver* s)
+{
+    return s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
+}
+
+bool auto_single(const Solver* s)
+{
+    if (s->eq_mode == 2) return false;
+    return s->D == 3 ? elbm::single_tmem_geometry(*s) : !bounded_solver(s);
+}
+
 int effective_kernel(const Solver* s)
 {
     if (s->eq_mode == 2) return 1;
-    if (s->kernel == 0) return (s->f2 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
-    const bool bounded = s->walls_y || s->g[0] != 0.0 || s->g[1] != 0.0 || s->g[2] != 0.0;
-    if (!bounded) return s->kernel;
+    if (s->kernel == 0) return (s->f2 && auto_single(s)) ? 3 : 1;
+    if (!bounded_solver(s)) return s->kernel;
     return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
 }
 
@@ -196,7 +212,7 @@ int ensure_second_array(elbm_solver* s, int kernel)
         return ELBM_OK;
     }
     if (s->f2) return ELBM_OK;
-    if (kernel == 0 && !elbm::single_tmem_geometry(*s)) return ELBM_OK;
+    if (kernel == 0 && !(s->D == 2 || elbm::single_tmem_geometry(*s))) return ELBM_OK;
     cudaError_t e = cudaMallocAsync(&s->f2, population_bytes(s), s->stream);
     if (e != cudaSuccess) {
         s->f2 = nullptr;
@@ -307,7 +323,6 @@ int elbm_set_option(elbm_solver* s, int key, double value)
         case ELBM_OPT_KERNEL: {
             if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
                 return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2 or 3");
-            if (value == 3.0 && s->D != 3) return fail(ELBM_ERR_ARG, "the single-pass kernel is D3Q27 only");
             const int rc = ensure_second_array(s, (int)value);
             if (rc != ELBM_OK) return rc;
             s->kernel = (int)value;
@@ -428,7 +443,8 @@ int elbm_step(elbm_solver* s, int n)
     while (left > 0 && e == cudaSuccess) {
         if (kernel == 3 && s->parity == 0 && s->f2) {
             // single pass: own-location state in f, result in f2, then swap
-            e = elbm::step_single_impl<3>(*s, s->f2, &s->launches);
+            e = (s->D == 2) ? elbm::step_single_impl<2>(*s, s->f2, &s->launches)
+                            : elbm::step_single_impl<3>(*s, s->f2, &s->launches);
             std::swap(s->f, s->f2);
             --left;
         } else if (kernel == 2) {

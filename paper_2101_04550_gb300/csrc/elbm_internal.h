@@ -101,11 +101,14 @@ void fill_params(const Solver& s, StepParams& p);
 template <int D> cudaError_t step_two_pass_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
+template <> cudaError_t step_single_impl<2>(const Solver&, void*, long long*);  // kernels_d2q9.cu
 bool single_tmem_geometry(const Solver& s);
 int single_pass_variant(const Solver& s);
 // Kernel form a step of s uses (1 two-pass, 2 graph-pipelined, 3 single pass):
 // the requested form where it applies, else the two-pass form.
 int effective_kernel(const Solver* s);
+// Whether the automatic form steps s in the single pass (given its second array).
+bool auto_single(const Solver* s);
 template <int D> cudaError_t build_step_graph_impl(const Solver&, int, cudaGraphExec_t*, int*);
 template <int D> cudaError_t init_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t moments_impl(const Solver&, void*, void*, int, long long*);
@@ -115,6 +118,16 @@ template <int D> cudaError_t reduce_impl(const Solver&, long long*);
 template <int D> cudaError_t mode_sums_impl(const Solver&, const double*, const double*, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
 template <int D> cudaError_t batch_enqueue_impl(int, int, int, int, cudaStream_t, long long*);
+// Flattened single-pass batch (batch_single.cuh): size of one member record,
+// filling the record of solver s (s.f as array 0, s.f2 as array 1; tensor
+// maps re-encoded when encode_maps), and enqueueing nsteps launches of the
+// batch kernel over a work list of nwork items (x member, y x0, z y0,
+// w z0 | z1 << 16) in device memory.
+size_t sp_member_bytes();
+cudaError_t sp_member_fill(const Solver& s, void* record, bool encode_maps);
+void sp_member_set_phase(void* record, int phase);
+cudaError_t sp_batch_enqueue(int storage, bool bc, bool fx, const void* members, const void* work, int nwork,
+                             int nsteps, cudaStream_t st, long long* launches);
 template <int D> cudaError_t batch_upload_impl(int, const BatchMember*, int, cudaStream_t);
 
 }  // namespace elbm

@@ -3,6 +3,7 @@
 #include "single_pass_tmem.cuh"
 #include "graph_step.cuh"
 #include "batch.cuh"
+#include "batch_single.cuh"
 
 namespace elbm {
 template cudaError_t step_two_pass_impl<3>(const Solver&, int, long long*);
@@ -24,10 +25,11 @@ bool single_tmem_geometry(const Solver& s)
 }
 // Single-pass kernel a step of s launches (the arrays are 16-byte aligned, as
 // the stream-ordered allocator returns them): 1 TMEM (32 x 16 tiles), 2 TMA
-// (32 x 8 tiles), 3 cp.async-staged.  Walls and the body force run in the
-// TMEM kernel only.
+// (32 x 8 tiles), 3 cp.async-staged; 4 the D2Q9 row march.  Walls and the
+// body force run in the TMEM kernel only.
 int single_pass_variant(const Solver& s)
 {
+    if (s.D == 2) return 4;
     if (single_tmem_geometry(s)) return 1;
     const bool fast = s.nx % kTileX == 0 && s.ny % kTileY == 0 && (s.nx * (int)storage_bytes(s.storage)) % 16 == 0;
     return fast ? 2 : 3;

@@ -81,7 +81,7 @@ struct TmemLayout {
 // anomaly's negated ghost value in the central difference) and the body force,
 // read from the parameter block as in the two-pass kernels; with neither set
 // in p it computes the same bits as BC = false.
-template <int ST, bool BC>
+template <int ST, bool BC, bool FX = false>
 __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const CUtensorMap* tm_row,
                                                const StepParams& p, void* dst, int x0, int y0, int z0, int z1,
                                                unsigned char* smem_raw)
@@ -219,15 +219,15 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
         float* qys = reinterpret_cast<float*>(base + L::off_qy);
         auto QX = [&](int s, int y, int x) -> float& { return qxs[(s * kTmTileY + y) * (kTileX + 2) + x]; };
         auto QY = [&](int s, int y, int x) -> float& { return qys[(s * (kTmTileY + 2) + y) * kTileX + x]; };
-        auto anomaly_m = [&](auto&& gval, float* q, float& drho, float* j) {
+        auto anomaly_m = [&](auto&& gval, float* q, float& drho, float* j, float& inv_rho) {
             moments_of<3>(p, gval, drho, j);
-            const float inv_rho = 1.0f / (p.rho_ref + drho);
+            inv_rho = 1.0f / (p.rho_ref + drho);
 #pragma unroll
             for (int a = 0; a < 3; ++a) q[a] = anomaly(p, a, j[a], j[a] * inv_rho);
         };
         auto anomaly_of = [&](auto&& gval, float* q) {
-            float drho, j[3];
-            anomaly_m(gval, q, drho, j);
+            float drho, j[3], inv_rho;
+            anomaly_m(gval, q, drho, j, inv_rho);
         };
         // TMEM columns of this thread: its warp's lane quarter; 32 columns per
         // warp of the quarter (warps w, w+4, w+8, w+12 share a quarter); 128 per plane slot
@@ -239,12 +239,12 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
 
         float qz_prev = 0.f, qz_cur = 0.f;
         // moments of the own node of the plane relaxed next (computed with its anomaly)
-        float m_drho = 0.f, m_j[3] = {0.f, 0.f, 0.f};
+        float m_drho = 0.f, m_j[3] = {0.f, 0.f, 0.f}, m_inv_rho = 1.f;
         for (int k = 0; k < K; ++k) {
             const int b = k % L::ntile, r = k & 1, s = k % kTmaQSlots;
             const bool got = wait(full_t(b), (k / L::ntile) & 1) && wait(full_r(r), (k / 2) & 1);
             if (!__all_sync(0xffffffffu, got)) break;
-            float q[3], k_drho, k_j[3];
+            float q[3], k_drho, k_j[3], k_inv_rho;
             {
                 const T* own = tile + b * 27 * kPlaneElems + ty * kTileX + tx;
                 float g[27];
@@ -252,7 +252,7 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
                 for (int i = 0; i < 27; ++i) g[i] = raw_value<ST>(p, own[i * kPlaneElems], i);
                 mbar_arrive(empty_t(b));
                 if (k >= 1 && k < K - 1) tmem_store27(t_own + (uint32_t)((k & 1) * 128), g);
-                anomaly_m([&](int i) { return g[i]; }, q, k_drho, k_j);
+                anomaly_m([&](int i) { return g[i]; }, q, k_drho, k_j, k_inv_rho);
             }
             QX(s, ty, tx + 1) = q[0];
             QY(s, ty + 1, tx) = q[1];
@@ -285,6 +285,7 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
             if (k == 1) {
                 qz_cur = q[2];
                 m_drho = k_drho;
+                m_inv_rho = k_inv_rho;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) m_j[a] = k_j[a];
                 continue;
@@ -324,10 +325,12 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
                     S::store(out + slot, v);
                 }
             };
-            relax_streamed<3, false, BC>(p, gval, put, drho, j, d);
+            // (the walls-and-force kernel recomputes it: one register fewer across the loop)
+            relax_streamed<3, false, BC, FX>(p, gval, put, drho, j, d, BC ? 0.f : m_inv_rho);
             qz_prev = qz_cur;
             qz_cur = qz_next;
             m_drho = k_drho;
+            m_inv_rho = k_inv_rho;
 #pragma unroll
             for (int a = 0; a < 3; ++a) m_j[a] = k_j[a];
         }
@@ -343,16 +346,17 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
 }
 
 // The single-pass step of one grid: block (bx, by, bz) takes the tile column
-// at (32 bx, 16 by), planes kSegPlanes bz onwards.
-template <int ST, bool BC = false>
+// at (32 bx, 16 by), planes kSegPlanes bz onwards.  FX (with BC): the body
+// force acts along x alone.
+template <int ST, bool BC = false, bool FX = false>
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_single_pass_tmem(const __grid_constant__ CUtensorMap tm_tile, const __grid_constant__ CUtensorMap tm_row,
                        const __grid_constant__ StepParams p, void* dst)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z0 = blockIdx.z * kSegPlanes;
-    tmem_tile_step<ST, BC>(&tm_tile, &tm_row, p, dst, blockIdx.x * kTileX, blockIdx.y * kTmTileY, z0,
-                           min(p.nz, z0 + kSegPlanes), smem_raw);
+    tmem_tile_step<ST, BC, FX>(&tm_tile, &tm_row, p, dst, blockIdx.x * kTileX, blockIdx.y * kTmTileY, z0,
+                               min(p.nz, z0 + kSegPlanes), smem_raw);
 }
 
 template <int ST>
@@ -363,7 +367,7 @@ bool single_tmem_ok(const Solver& s, const void* src, const void* dst)
            ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0);
 }
 
-template <int ST, bool BC = false>
+template <int ST, bool BC = false, bool FX = false>
 cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, bool* launched)
 {
     *launched = false;
@@ -371,11 +375,12 @@ cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, 
     CUtensorMap tm_tile, tm_row;
     if (encode_population_maps(s, p.f, kTmTileY, &tm_tile, &tm_row) != cudaSuccess) return cudaSuccess;
     const int smem = TmemLayout<ST>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_single_pass_tmem<ST, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_single_pass_tmem<ST, BC, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(s.nx / kTileX), (unsigned)(s.ny / kTmTileY),
                     (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
-    k_single_pass_tmem<ST, BC><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, p, dst);
+    k_single_pass_tmem<ST, BC, FX><<<grid, kTmThreads, smem, s.stream>>>(tm_tile, tm_row, p, dst);
     *launched = true;
     return cudaGetLastError();
 }
@@ -402,8 +407,11 @@ cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
         ELBM_DISPATCH_STORAGE(s.storage, {
             bool done = false;
             if (p.walls_y || p.forced) {
-                // walls and body force: the TMEM form only (the caller checks its geometry)
-                e = launch_single_tmem<ST, true>(s, p, dst, &done);
+                // walls and body force: the TMEM form only (the caller checks its geometry);
+                // a force along x alone (or none) takes the lighter force increment
+                const bool fx = p.g[1] == 0.f && p.g[2] == 0.f;
+                e = fx ? launch_single_tmem<ST, true, true>(s, p, dst, &done)
+                       : launch_single_tmem<ST, true, false>(s, p, dst, &done);
                 if (e == cudaSuccess && !done) e = cudaErrorNotSupported;
                 if (e == cudaSuccess) ++*launches;
                 return e;

@@ -2,6 +2,7 @@
 // lattice dimension D, the storage mode ST and (for the hot kernels) the AA
 // streaming parity PAR.  Included by one translation unit per lattice.
 #pragma once
+#include <type_traits>
 #include <cfloat>
 
 #include "lbm_device.cuh"
@@ -75,14 +76,16 @@ __device__ __forceinline__ void moments_of(const StepParams& p, G&& gval, float&
 // POLY selects the conventional second-order equilibrium instead.  BC adds
 // the body-force increment F_i (ForceIncrement) when p.forced is set; it is
 // kept out of the conservation moments, so the node gains exactly the
-// momentum rho g of the force.
-template <int D, bool POLY = false, bool BC = false, typename G, typename P>
+// momentum rho g of the force.  FX: the force is known to act along x alone
+// (ForceIncrementX, same bits, fewer registers).  inv_rho, if given (> 0),
+// is the caller's 1 / (rho_ref + drho), the very value computed here otherwise.
+template <int D, bool POLY = false, bool BC = false, bool FX = false, typename G, typename P>
 __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&& put, float drho,
-                                               const float* j, const float* d)
+                                               const float* j, const float* d, float inv_rho_in = 0.f)
 {
     constexpr int I0 = (Lat<D>::Q - 1) / 2;
     const float rho = p.rho_ref + drho;
-    const float inv_rho = 1.0f / rho;
+    const float inv_rho = inv_rho_in > 0.f ? inv_rho_in : 1.0f / rho;
     float u[3], pcorr[3], du[3], dP[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -92,7 +95,7 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     baseline_args<D>(p, u, pcorr, du, dP);
     const float om = p.omega;
     const bool forced = BC && p.forced;
-    ForceIncrement<D> frc;
+    typename std::conditional<FX, ForceIncrementX<D>, ForceIncrement<D>>::type frc;
     if (forced) frc.init(p, rho / om, u);
     float e0 = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
     float keep[2 * D + 1], kf[2 * D + 1];

@@ -36,7 +36,8 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_steps_done", "elbm_omega", "elbm_device_bytes", "elbm_launch_count", "elbm_get_u_ref",
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
            "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
-           "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums", "elbm_kernel_form"]
+           "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums", "elbm_kernel_form",
+           "elbm_batch_tuning", "elbm_batch_set_config"]
 
 
 class ElbmError(RuntimeError):
@@ -85,6 +86,9 @@ def load(build_if_missing: bool = True):
         L.elbm_mode_sums.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)]
         L.elbm_kernel_form.argtypes = [vp, ctypes.POINTER(ip)]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
+        L.elbm_batch_tuning.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                         ctypes.POINTER(dp)]
+        L.elbm_batch_set_config.argtypes = [vp, ip]
         L.elbm_batch_add.argtypes = [vp, vp]
         L.elbm_batch_remove.argtypes = [vp, vp]
         L.elbm_batch_size.argtypes = [vp]
@@ -319,6 +323,22 @@ class Batch:
         launches = ctypes.c_longlong()
         _check(load().elbm_batch_info(self._h, ctypes.byref(bs), ms, ctypes.byref(launches)))
         return {"block_size": bs.value, "tuned_ms": {128: ms[0], 256: ms[1]}, "launches": launches.value}
+
+    def set_config(self, config):
+        """Single-pass batches: pin the configuration (0..5 flattened launch,
+        6 per-member graphs) or return to the autotuner (-1)."""
+        _check(load().elbm_batch_set_config(self._h, int(config)))
+
+    def tuning(self):
+        """Single-pass batches: the configuration of the last step and the
+        autotuner's two-step timings (ms, -1 for a candidate not yet timed)."""
+        c, seg, inter = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 7)()
+        rc = load().elbm_batch_tuning(self._h, ctypes.byref(c), ctypes.byref(seg), ctypes.byref(inter), ms)
+        if rc < 0:
+            _check(rc)
+        return {"config": c.value, "seg_planes": seg.value, "interleaved": bool(inter.value),
+                "member_graphs": c.value == 6, "tuned": rc == 0, "ms": list(ms)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -7,9 +7,11 @@ requests whenever the HBM budget and the slot limit allow, and advances all
 resident solves together in chunks of steps with the batched step of the
 library, one batch for every group of requests that share lattice, storage
 mode and kernel form: D3Q27 grids the single pass takes (x a multiple of 32
-nodes, y of 16) run in it, one CUDA graph per request replayed side by side;
-the others run in the two-pass form, one CUDA graph of two launches per step
-for the whole group.  Requests that arrive while others run join at the next
+nodes, y of 16) run in it, one launch per step of the flattened single-pass
+kernel over every such request of the group (or per-request graphs, if the
+library's autotuner finds them faster for the group's size); the others run
+in the two-pass form, one CUDA graph of two launches per step for the whole
+group.  Requests that arrive while others run join at the next
 chunk boundary; finished ones are read out and freed.  The "plain" mode
 serves the same trace one request at a time in arrival order, in the same
 kernel forms, with per-step launches and no graphs.
@@ -138,16 +140,21 @@ class Server:
     kernels           "auto": the single-pass form for the grids it takes, the
                       two-pass form for the rest; "two-pass": the two-pass form
                       for every request
+    sp_config         configuration of the single-pass batches (None: the
+                      library's autotuner; 0..5 the flattened launch, 6
+                      per-member graphs -- see elbm_batch_set_config)
     clock             callable giving seconds (wall clock by default)
     """
 
     def __init__(self, hbm_budget=8 << 30, chunk_steps=100, max_active=64, clock=time.perf_counter,
-                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=8 << 20, kernels="auto"):
+                 stream=None, sleep=time.sleep, policy="fifo", step_floor_nodes=8 << 20, kernels="auto",
+                 sp_config=None):
         if policy not in ("fifo", "srpt"):
             raise ValueError("policy must be 'fifo' or 'srpt'")
         if kernels not in ("auto", "two-pass"):
             raise ValueError("kernels must be 'auto' or 'two-pass'")
         self.kernels = kernels
+        self.sp_config = sp_config
         self.hbm_budget = int(hbm_budget)
         self.chunk_steps = int(chunk_steps)
         self.max_active = int(max_active)
@@ -276,6 +283,8 @@ class Server:
                 if not a.in_batch:
                     if a.key not in batches:
                         batches[a.key] = elbm.Batch([a.solver])
+                        if a.form == 3 and self.sp_config is not None:
+                            batches[a.key].set_config(self.sp_config)
                     else:
                         batches[a.key].add(a.solver)
                     a.in_batch = True

@@ -125,9 +125,53 @@ def test_single_pass_batch_matches_solo_bitwise(storage):
         b.step(10)
         b.step(10)
         info = b.info()
-    assert info["block_size"] == 0 and info["launches"] == 27 * len(SPECS_SP)
+        tuning = b.tuning()
+    # every candidate of the autotuner ran two real steps of these members
+    assert info["block_size"] == 0 and tuning["tuned"] and min(tuning["ms"]) > 0
     for s, m in zip(solo, mixed):
         assert m.steps_done == s.steps_done == 27
+        assert np.array_equal(s.get_populations(), m.get_populations())
+
+
+@pytest.mark.parametrize("config", range(7))
+def test_single_pass_batch_every_configuration_bitwise(config):
+    """Each configuration of the single-pass batch -- the flattened launch
+    with 32-, 16- or 8-plane segments, members one after another or
+    interleaved, and per-member graphs -- pinned, over odd and even step
+    counts, with a member whose grid the TMEM kernel does not take (32 x 8
+    TMA tiles, always per-member graphs) beside them: bit for bit the solo
+    states; the flattened configurations make one launch per step."""
+    specs = SPECS_SP + [((32, 8, 16), (1.0, 1.0, 1.0), 0.4, 0.02)]
+    solo = [_make_sp(sp, elbm.F16_SHIFT, k) for k, sp in enumerate(specs)]
+    mixed = [_make_sp(sp, elbm.F16_SHIFT, k) for k, sp in enumerate(specs)]
+    assert mixed[-1].kernel_form == (3, 2)
+    for s in solo:
+        s.step(16)
+    with elbm.Batch(mixed) as b:
+        b.set_config(config)
+        before = b.info()["launches"]
+        b.step(5)
+        b.step(11)
+        launches = b.info()["launches"] - before
+        assert b.tuning()["config"] == config
+    flat_launches = 16 if config < 6 else 16 * len(SPECS_SP)
+    assert launches == flat_launches + 16  # + the TMA member's own launches
+    for s, m in zip(solo, mixed):
+        assert np.array_equal(s.get_populations(), m.get_populations())
+
+
+def test_single_pass_batches_live_side_by_side():
+    """Two single-pass batches of the same storage mode at once (the member
+    tables live in each batch's device memory), stepped alternately."""
+    solo = [_make_sp(sp, elbm.F32_SHIFT, k) for k, sp in enumerate(SPECS_SP)]
+    mixed = [_make_sp(sp, elbm.F32_SHIFT, k) for k, sp in enumerate(SPECS_SP)]
+    for s in solo:
+        s.step(9)
+    with elbm.Batch(mixed[:2]) as b1, elbm.Batch(mixed[2:]) as b2:
+        for k in (3, 6):
+            b1.step(k)
+            b2.step(k)
+    for s, m in zip(solo, mixed):
         assert np.array_equal(s.get_populations(), m.get_populations())
 
 

@@ -180,15 +180,17 @@ TMEM_N = (64, 32, 20)
 
 @pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT, elbm.F16_SHIFT])
 @pytest.mark.parametrize("steps", [1, 2, 7])
-def test_single_pass_walls_and_force_bitwise(storage, steps):
+@pytest.mark.parametrize("force", [(2e-5, 0, 0), (2e-5, -1e-5, 3e-5)])
+def test_single_pass_walls_and_force_bitwise(storage, steps, force):
     """The TMEM single pass with walls and body force (nx a multiple of 32,
     ny of 16) against the two-pass form: bit-identical populations, rest
-    storage baseline, both parities."""
+    storage baseline, both parities; a force along x alone (the lighter force
+    increment of the single pass) and along all three axes."""
     rho, u = inputs.channel(TMEM_N, CHANNEL_LAM, u_center=0.05, perturbation=0.05, seed=3)
     out = []
     for kernel in (1, 3):
         with elbm.Solver(elbm.D3Q27, TMEM_N, stretch=CHANNEL_LAM, T=CHANNEL_T, nu=0.02, storage=storage,
-                         kernel=kernel, walls_y=True, force=(2e-5, 0, 0)) as s:
+                         kernel=kernel, walls_y=True, force=force) as s:
             s.init(rho, u)
             s.step(steps)
             out.append(s.get_populations())

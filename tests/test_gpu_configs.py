@@ -96,14 +96,17 @@ def test_viscosity_independent_of_advection_on_gpu(T):
 
 @pytest.mark.parametrize("n,lam", [((1024, 1024), (1.0, 1.0)), ((1024, 512), (1.0, 2.0))])
 @pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT])
-def test_double_shear_layer_full_size(n, lam, storage):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_double_shear_layer_full_size(n, lam, storage, kernel):
     """D2Q9 double shear layer at full size, cubic and stretched (dy/dx = 2),
     T = 0.5, U = 0.2, Re = 3e4 (nu = U L / Re, L = 1024), 21 steps (both
-    parities), every node against the oracle."""
+    parities), every node against the oracle; the automatic form (the row-march
+    single pass the benchmark times) and the two-pass form."""
     U, Re, T, steps = 0.2, 3e4, 0.5, 21
     nu = U * 1024 / Re
     rho, u = inputs.double_shear_layer(n, U=U)
-    with elbm.Solver(elbm.D2Q9, n, stretch=lam, T=T, nu=nu, storage=storage) as s:
+    with elbm.Solver(elbm.D2Q9, n, stretch=lam, T=T, nu=nu, storage=storage, kernel=kernel) as s:
+        assert s.kernel_form == ((3, 4) if kernel == 0 else (1, 0))
         s.init(rho, u)
         s.step(steps)
         _, ug = s.moments()

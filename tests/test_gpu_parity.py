@@ -52,7 +52,7 @@ def _gpu():
 
 # ------------------------------------------------------------ D2Q9 cases
 @pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT])
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_d2q9_shear_wave_64_1000_steps(storage, kernel):
     """D2Q9 advected shear wave, 64x64 periodic, T = 1/3, u_x = 0.1,
     u_y = 1e-3 sin(2 pi x / 64), nu = 0.01, 1000 steps."""
@@ -65,7 +65,7 @@ def test_d2q9_shear_wave_64_1000_steps(storage, kernel):
     assert rel_linf(ug[1], uo[1]) <= 20 * TOL[storage]
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("T", [1 / 3, 0.5])
 def test_d2q9_rotated_stretched_correction_active(kernel, T):
     """Rotated wave on a lam_x = 2 lattice: the central-difference correction
@@ -108,13 +108,14 @@ def test_second_order_equilibrium_mode(lattice, n, lam):
     assert rel_linf(ug, uo) <= 1e-5
 
 
+@pytest.mark.parametrize("kernel", [1, 3])
 @pytest.mark.parametrize("storage", [elbm.F16_SHIFT, elbm.BF16_SHIFT])
-def test_d2q9_half_storage_advected(storage):
+def test_d2q9_half_storage_advected(storage, kernel):
     """Half-precision storage of an advected rotated wave (U = 0.1, amplitude
     1e-2), with the storage baseline at the field's mean velocity."""
     n = (64, 64)
     rho, u, _, _ = inputs.shear_wave(n, (1.0, 1.0), (1, 1), (-1, 1), 1e-2, 0.1)
-    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, 1, u_ref="mean")
+    _, ug = run_gpu(elbm.D2Q9, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000, storage, kernel, u_ref="mean")
     _, uo = run_oracle(2, n, (1.0, 1.0), 1 / 3, 0.01, rho, u, 1000)
     assert rel_linf(ug, uo) <= TOL[storage]
 
@@ -189,7 +190,7 @@ def test_kernel_forms_agree_bitwise(lattice, n, storage):
         rho, u = inputs.double_shear_layer(n, U=0.1)
     lam = (1.0, 2.0, 1.0)
     outs = []
-    for kernel in ((1, 2, 3) if D == 3 else (1, 2)):
+    for kernel in (1, 2, 3):
         with elbm.Solver(lattice, n, stretch=lam, T=0.5, nu=0.01, storage=storage, kernel=kernel) as s:
             s.init(rho, u)
             for k in (1, 2, 4):

@@ -120,7 +120,10 @@ def test_tmem_single_pass_1000_steps_walls_and_force(storage):
     (elbm.D3Q27, (64, 32, 32), {"equilibrium": 2}, (1, 0)),       # second order: two-pass only
     (elbm.D3Q27, (48, 48, 48), {}, (1, 0)),                       # x not a multiple of 32
     (elbm.D3Q27, (32, 8, 16), {}, (1, 0)),                        # y not a multiple of 16
-    (elbm.D2Q9, (64, 64), {}, (1, 0)),
+    (elbm.D2Q9, (64, 64), {}, (3, 4)),                             # D2Q9: the row-march single pass
+    (elbm.D2Q9, (33, 5), {}, (3, 4)),
+    (elbm.D2Q9, (64, 64), {"walls_y": True}, (1, 0)),             # walls: two-pass (no D2Q9 single pass)
+    (elbm.D2Q9, (64, 64), {"equilibrium": 2}, (1, 0)),
     (elbm.D3Q27, (32, 8, 16), {"kernel": 3}, (3, 2)),             # requested: 32 x 8 TMA tiles
     (elbm.D3Q27, (37, 20, 23), {"kernel": 3}, (3, 3)),            # requested: cp.async-staged
     (elbm.D3Q27, (37, 20, 23), {"kernel": 3, "walls_y": True}, (1, 0)),
