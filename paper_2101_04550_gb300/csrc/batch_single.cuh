@@ -63,8 +63,7 @@ template <int ST, bool BC, bool FX>
 cudaError_t sp_batch_launch(const SpMember* members, const int4* work, int nwork, int nsteps, cudaStream_t st)
 {
     const int smem = TmemLayout<ST>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_single_pass_tmem_batch<ST, BC, FX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem_limit_once<k_single_pass_tmem_batch<ST, BC, FX>>(smem);
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
         k_single_pass_tmem_batch<ST, BC, FX><<<nwork, kTmThreads, smem, st>>>(members, work, k);
         e = cudaGetLastError();

@@ -78,6 +78,13 @@ struct Solver {
     long long launches = 0;
     size_t bytes = 0;
     long long uid = 0;                // unique per solver of the process (never reused)
+    // tensor maps of the TMA-fed single-pass kernels, cached per population
+    // array and tile height (tma_maps.cu); a map depends only on the array's
+    // address and the grid, so a cached one stays valid for that address
+    alignas(64) mutable unsigned char tmap[2][2][128] = {};
+    mutable const void* tmap_f[2] = {nullptr, nullptr};
+    mutable int tmap_tile_y[2] = {0, 0};
+    mutable int tmap_next = 0;
 };
 
 // One member of a batch (see batch.cuh).

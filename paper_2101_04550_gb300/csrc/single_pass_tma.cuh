@@ -27,6 +27,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <atomic>
+
 #include "single_pass.cuh"
 
 namespace elbm {
@@ -386,8 +388,25 @@ bool single_tma_ok(const Solver& s, const void* src, const void* dst)
 }
 
 // Tensor maps of one population array: dims (x, y, z, population), boxes of
-// the tile (32 x tile_y x 1 x 27) and of one ring row (32 x 1 x 1 x 27).
+// the tile (32 x tile_y x 1 x 27) and of one ring row (32 x 1 x 1 x 27);
+// cached in the solver per array and tile height.
 cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row);
+
+// Raise kernel K's dynamic shared-memory limit to `bytes`, once per device
+// and process.
+template <auto K>
+cudaError_t set_smem_limit_once(int bytes)
+{
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 template <int ST>
 cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, bool* launched)
@@ -398,7 +417,7 @@ cudaError_t launch_single_tma(const Solver& s, const StepParams& p, void* dst, b
     cudaError_t e = encode_population_maps(s, p.f, kTileY, &tm_tile, &tm_row);
     if (e != cudaSuccess) return cudaSuccess;  // no TMA: the caller takes another single-pass kernel
     const int smem = TmaLayout<ST>::bytes;
-    e = cudaFuncSetAttribute(k_single_pass_tma<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = set_smem_limit_once<k_single_pass_tma<ST>>(smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(s.nx / kTileX), (unsigned)(s.ny / kTileY),
                     (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));

@@ -375,8 +375,7 @@ cudaError_t launch_single_tmem(const Solver& s, const StepParams& p, void* dst, 
     CUtensorMap tm_tile, tm_row;
     if (encode_population_maps(s, p.f, kTmTileY, &tm_tile, &tm_row) != cudaSuccess) return cudaSuccess;
     const int smem = TmemLayout<ST>::bytes;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_single_pass_tmem<ST, BC, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = set_smem_limit_once<k_single_pass_tmem<ST, BC, FX>>(smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)(s.nx / kTileX), (unsigned)(s.ny / kTmTileY),
                     (unsigned)((s.nz + kSegPlanes - 1) / kSegPlanes));
@@ -424,10 +423,10 @@ cudaError_t step_single_impl(const Solver& s, void* dst, long long* launches)
             }
             if (single_fast_ok<ST>(s)) {
                 const size_t fsmem = sizeof(FastSmem<ST>);
-                e = cudaFuncSetAttribute(k_single_pass_fast<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+                e = set_smem_limit_once<k_single_pass_fast<ST>>((int)fsmem);
                 if (e == cudaSuccess) k_single_pass_fast<ST><<<grid, kBlock, fsmem, s.stream>>>(p, dst);
             } else {
-                e = cudaFuncSetAttribute(k_single_pass<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = set_smem_limit_once<k_single_pass<ST>>((int)smem);
                 if (e == cudaSuccess) k_single_pass<ST><<<grid, kBlock, smem, s.stream>>>(p, dst);
             }
         });

@@ -3,6 +3,7 @@
 // the driver library.
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "elbm_internal.h"
@@ -30,10 +31,35 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 }  // namespace
 
+cudaError_t encode_uncached(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row);
+
+// The maps of array f: from the solver's cache (two arrays deep, keyed by
+// address and tile height), else encoded and cached.
+cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row)
+{
+    static_assert(sizeof(CUtensorMap) == 128, "a tensor map is 128 bytes");
+    for (int k = 0; k < 2; ++k)
+        if (s.tmap_f[k] == f && s.tmap_tile_y[k] == tile_y) {
+            std::memcpy(tile, s.tmap[k][0], sizeof(CUtensorMap));
+            std::memcpy(row, s.tmap[k][1], sizeof(CUtensorMap));
+            return cudaSuccess;
+        }
+    const cudaError_t e = encode_uncached(s, f, tile_y, tile, row);
+    if (e == cudaSuccess) {
+        const int k = s.tmap_next;
+        s.tmap_next ^= 1;
+        std::memcpy(s.tmap[k][0], tile, sizeof(CUtensorMap));
+        std::memcpy(s.tmap[k][1], row, sizeof(CUtensorMap));
+        s.tmap_f[k] = f;
+        s.tmap_tile_y[k] = tile_y;
+    }
+    return e;
+}
+
 // Layout f[i][z][y][x] as a 4-D tensor (x, y, z, i) of 4- or 2-byte elements;
 // boxes of 32 x tile_y x 1 x 27 (the tile of one plane) and 32 x 1 x 1 x 27 (one
 // ring row).  Strides are multiples of 16 bytes when nx * element size is.
-cudaError_t encode_population_maps(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row)
+cudaError_t encode_uncached(const Solver& s, const void* f, int tile_y, CUtensorMap* tile, CUtensorMap* row)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn || s.D != 3) return cudaErrorNotSupported;
