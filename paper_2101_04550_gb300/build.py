@@ -1,7 +1,9 @@
 """Build the elbm CUDA library in-tree: ``_build/libelbm.so`` for sm_103a.
 
 One nvcc process per translation unit (run in parallel), then a shared-library
-link.  Rebuilds only when a source or header is newer than the library.
+link.  Rebuilds only when a source or header is newer than the library, and
+then recompiles only the translation units whose own dependencies (the .d
+files nvcc writes next to each object) changed.
 """
 from __future__ import annotations
 
@@ -17,8 +19,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libelbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# nvcc runs from this directory with relative paths, so that the dependency
+# files it writes stay valid when the tree is copied elsewhere
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+         "--expt-relaxed-constexpr", "-I", os.path.join("..", "include")]
 
 
 def nvcc() -> str:
@@ -40,6 +44,28 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
+def _deps(dep_file: str):
+    """Files listed in an nvcc dependency file (make syntax), or None."""
+    try:
+        with open(dep_file) as fh:
+            text = fh.read().replace("\\\n", " ")
+    except OSError:
+        return None
+    _, _, rhs = text.partition(":")
+    return [t for t in rhs.split() if t]
+
+
+def _stale(src: str, obj: str) -> bool:
+    if not os.path.exists(obj):
+        return True
+    deps = _deps(obj[:-2] + ".d")
+    if deps is None:
+        return True
+    t = os.path.getmtime(obj)
+    paths = [d if os.path.isabs(d) else os.path.join(HERE, d) for d in deps] + [src, __file__]
+    return any(not os.path.exists(d) or os.path.getmtime(d) > t for d in paths)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and up_to_date():
         return LIB
@@ -51,10 +77,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     for src in sources:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+        if not force and not extra_flags and not _stale(src, obj):
+            continue
+        rel_src, rel_obj = os.path.relpath(src, HERE), os.path.relpath(obj, HERE)
+        cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-MD", "-MF", rel_obj[:-2] + ".d", "-c", rel_src, "-o", rel_obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, cwd=HERE)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()

@@ -729,6 +729,10 @@ int elbm_batch_remove(elbm_batch* b, elbm_solver* s)
     if (b->form == 3) {
         const cudaError_t e = retire_graphs(b, s->uid, 0);
         if (e != cudaSuccess) return bcuda(e, "elbm_batch_remove");
+        // its flattened-launch record (the next upload rebuilds the table without it)
+        b->sp_cache.erase(std::remove_if(b->sp_cache.begin(), b->sp_cache.end(),
+                                         [&](const elbm_batch::SpCached& c) { return c.uid == s->uid; }),
+                          b->sp_cache.end());
     }
     b->members.erase(it);
     return ELBM_OK;

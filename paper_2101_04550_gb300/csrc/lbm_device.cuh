@@ -293,10 +293,7 @@ __device__ __forceinline__ float anomaly(const StepParams& p, int a, float ja, f
 // delta_0 = -dP/lam^2 and delta_{+-1} = (+-du/lam + dP/lam^2)/2, so
 //   Psi_i - b_i = sum_a (prod_{b<a} base_b) delta_a (prod_{b>a} Psi_b)
 // is formed without cancellation, and rho Psi_i - rho_ref b_i =
-// (rho - rho_ref) Psi_i + rho_ref (Psi_i - b_i).  With the z factor taken
-// out of the first two terms, per (cx, cy) pair K = (rho - rho_ref) Pxy +
-// rho_ref (Pxy - bxy) is formed once and each population costs
-// A_z K + rho_ref bxy delta_z (two operations).  fn sees the populations
+// (rho - rho_ref) Psi_i + rho_ref (Psi_i - b_i).  fn sees the populations
 // with cz innermost, then cx, then cy (relax() and relax_streamed() sum the
 // increments along these lines).
 template <int D, typename F>
@@ -328,10 +325,12 @@ __device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float 
             if (D == 2) {
                 fn(cx + 3 * cy, fmaf(drho, pxy, dxy_r));
             } else {
-                const float kxy = fmaf(drho, pxy, dxy_r);
 #pragma unroll
-                for (int cz = 0; cz < 3; ++cz)
-                    fn(cx + 3 * cy + 9 * cz, fmaf(A[2][cz], kxy, p.bxy_r[cx + 3 * cy] * dl[2][cz]));
+                for (int cz = 0; cz < 3; ++cz) {
+                    const float psi = pxy * A[2][cz];
+                    const float dpsi_r = fmaf(dxy_r, A[2][cz], p.bxy_r[cx + 3 * cy] * dl[2][cz]);
+                    fn(cx + 3 * cy + 9 * cz, fmaf(drho, psi, dpsi_r));
+                }
             }
         }
     }

@@ -48,12 +48,23 @@ __global__ void __launch_bounds__(kD2Threads) k_single_pass_d2q9(const __grid_co
     float qy_m1 = 0.f, qy_m2 = 0.f;               // Q~_yyy of rows k-1 and k-2
 #pragma unroll
     for (int i = 0; i < 9; ++i) gp[i] = 0.f;
+    // raw populations of row k, loaded one row ahead so that the loads of row
+    // k + 1 are in flight while row k - 1 is relaxed
+    T raw[9];
+    {
+        const int node = wrapi(y0 - 1, p.ny) * p.nx + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) raw[i] = src[i * p.N + node];
+    }
     for (int k = 0; k < K; ++k) {
-        const int y = wrapi(y0 - 1 + k, p.ny);
-        const int node = y * p.nx + gx;
         float g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = raw_value<ST>(p, src[i * p.N + node], i);
+        for (int i = 0; i < 9; ++i) g[i] = raw_value<ST>(p, raw[i], i);
+        if (k + 1 < K) {
+            const int node = wrapi(y0 + k, p.ny) * p.nx + gx;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) raw[i] = src[i * p.N + node];
+        }
         float drho, j[3];
         moments_of<2>(p, [&](int i) { return g[i]; }, drho, j);
         const float inv = 1.0f / (p.rho_ref + drho);
