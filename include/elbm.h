@@ -233,10 +233,8 @@ long long elbm_launch_count(const elbm_solver* s);
  *  - two-pass members (periodic, unforced, extended or product-form
  *    equilibrium): one batched step is two launches (anomaly pass and collide
  *    pass of the two-pass form, Eqs. LBGK, Deviation, Paastar1, 27eqext) over
- *    all members, from a table of their parameters in constant memory,
- *    refreshed at every elbm_batch_step.  One live batch of this form per
- *    (lattice, storage mode) and device may exist at a time;
- *    elbm_batch_create returns ELBM_ERR_STATE for a second one;
+ *    all members, from a table of their parameters in device memory of the
+ *    batch, refreshed at every elbm_batch_step;
  *  - single-pass members (kernel form 3, D3Q27, two population arrays;
  *    walls and body force allowed where the single pass takes them): the
  *    members on the TMEM geometry (nx a multiple of 32, ny of 16) advance in
@@ -250,8 +248,8 @@ long long elbm_launch_count(const elbm_solver* s);
  *    on private streams of the batch, side by side -- the form other
  *    single-pass members (32 x 8 TMA or cp.async kernels) always take.  If any
  *    member has walls or a body force, the flattened launch uses the kernel
- *    that honours them for every member (same bits for the others).  Any
- *    number of single-pass batches may be live at once.
+ *    that honours them for every member (same bits for the others).
+ * Any number of batches, of either form, may be live at once.
  * Mixing the forms in one batch returns ELBM_ERR_ARG.
  */
 typedef struct elbm_batch elbm_batch;

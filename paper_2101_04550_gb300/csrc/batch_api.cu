@@ -4,11 +4,10 @@
 //
 // A batch has one of two forms, fixed by the kernel form of its members.
 //  * Two-pass members (form 1): the batched kernels read the member table from
-//    constant memory (one table per storage mode, refreshed before each launch
-//    sequence), so a live batch owns the table of its (lattice, storage) kind:
-//    one live batch of this form per kind and device.  A launch sequence of n
-//    steps is captured once as a CUDA graph; when membership changes the block
-//    total, the graph is re-captured and the executable graph updated in place.
+//    device memory of the batch, refreshed before each launch sequence.  A
+//    launch sequence of n steps is captured once as a CUDA graph; when
+//    membership changes the block total, the graph is re-captured and the
+//    executable graph updated in place.
 //  * Single-pass members (form 3, two population arrays each).  Members whose
 //    grids the TMEM single pass takes advance together in one launch per step
 //    of the flattened batch kernel (batch_single.cuh) over a work list of
@@ -28,8 +27,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -95,8 +92,9 @@ struct elbm_batch {
         size_t cap = 0;
         cudaEvent_t done = nullptr;    // recorded after the copy out of it
     };
-    Staging sp_stage[2][2];            // [table, work list][alternate buffers]
-    int sp_stage_next[2] = {0, 0};
+    Staging sp_stage[3][2];            // [single-pass table, work list, two-pass table][alternate buffers]
+    int sp_stage_next[3] = {0, 0, 0};
+    void* tp_table_dev = nullptr;      // two-pass member table (kBatchMax records)
     int sp_pinned = -1;                // configuration set by elbm_batch_set_config (-1: the autotuner's)
     int sp_config = -1;                // configuration of the last flattened call
     long long sp_key = -1;             // its tuning key
@@ -117,8 +115,6 @@ int bcuda(cudaError_t e, const char* what)
 // batch of the process: the first batch of a kind pays the two tuning steps.
 std::mutex g_tune_lock;
 std::map<std::pair<int, int>, int> g_tuned;
-// Kinds (device, lattice, storage) with a live batch: each owns a constant table.
-std::set<std::tuple<int, int, int>> g_live;
 
 void drop_graphs(elbm_batch* b)
 {
@@ -301,7 +297,8 @@ long long sp_key(const elbm_batch* b, const std::vector<elbm_solver*>& flat)
 }
 
 // Enqueue the copy of `bytes` from src to dev on the batch's private stream
-// through pinned staging buffer pair `which` (0 table, 1 work list), so that
+// through pinned staging buffer pair `which` (0 single-pass table, 1 work
+// list, 2 two-pass table), so that
 // the copy does not make the host wait for the stream; a buffer is reused
 // once the copy out of it two uploads ago has run.
 cudaError_t staged_upload(elbm_batch* b, int which, void* dev, const void* src, size_t bytes)
@@ -589,14 +586,16 @@ cudaError_t upload(elbm_batch* b)
     }
     b->blocks[0] = (int)begin128;
     b->blocks[1] = (int)begin256;
-    return (b->D == 2) ? elbm::batch_upload_impl<2>(b->storage, b->table.data(), (int)n, b->exec_stream)
-                       : elbm::batch_upload_impl<3>(b->storage, b->table.data(), (int)n, b->exec_stream);
+    return staged_upload(b, 2, b->tp_table_dev, b->table.data(), n * sizeof(elbm::BatchMember));
 }
 
 cudaError_t enqueue(elbm_batch* b, int block_size, int grid, int nsteps)
 {
-    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, grid, nsteps, b->exec_stream, &b->launches)
-                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, grid, nsteps, b->exec_stream, &b->launches);
+    const int n = (int)b->members.size();
+    return (b->D == 2) ? elbm::batch_enqueue_impl<2>(b->storage, block_size, grid, nsteps, b->tp_table_dev, n,
+                                                     b->exec_stream, &b->launches)
+                       : elbm::batch_enqueue_impl<3>(b->storage, block_size, grid, nsteps, b->tp_table_dev, n,
+                                                     b->exec_stream, &b->launches);
 }
 
 void advance_members(elbm_batch* b, int nsteps)
@@ -694,14 +693,12 @@ int elbm_batch_create(elbm_solver* const* solvers, int n, elbm_batch** out)
     }
     {
         std::lock_guard<std::mutex> lock(g_tune_lock);
-        if (b->form == 1 && !g_live.insert({b->device, b->lattice, b->storage}).second) {
-            delete b;
-            return bfail(ELBM_ERR_STATE, "a batch of this lattice and storage mode is already live on this device");
-        }
         auto it = g_tuned.find({b->lattice, b->storage});
         if (b->form == 1 && it != g_tuned.end()) b->block_size = it->second;
     }
     cudaError_t e = cudaStreamCreateWithFlags(&b->exec_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && b->form == 1)
+        e = cudaMalloc(&b->tp_table_dev, sizeof(elbm::BatchMember) * elbm::kBatchMax);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -859,10 +856,7 @@ void elbm_batch_destroy(elbm_batch* b)
         cudaEventDestroy(b->pool_done[k]);
         cudaStreamDestroy(b->pool[k]);
     }
-    if (b->form == 1) {
-        std::lock_guard<std::mutex> lock(g_tune_lock);
-        g_live.erase({b->device, b->lattice, b->storage});
-    }
+    if (b->tp_table_dev) cudaFree(b->tp_table_dev);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->exec_stream) cudaStreamDestroy(b->exec_stream);

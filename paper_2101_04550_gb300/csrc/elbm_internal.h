@@ -94,7 +94,7 @@ struct BatchMember {
     int parity;           // streaming parity before the first step of a launch sequence
 };
 
-// Members of one batch at most (the constant-memory table of a storage mode).
+// Members of one batch at most.
 constexpr int kBatchMax = 40;
 
 size_t storage_bytes(int storage);
@@ -124,7 +124,8 @@ template <int D> cudaError_t set_populations_impl(const Solver&, const void*, in
 template <int D> cudaError_t reduce_impl(const Solver&, long long*);
 template <int D> cudaError_t mode_sums_impl(const Solver&, const double*, const double*, long long*);
 template <int D> cudaError_t field_sums_impl(const Solver&, const void*, const void*, int, long long*);
-template <int D> cudaError_t batch_enqueue_impl(int, int, int, int, cudaStream_t, long long*);
+template <int D>
+cudaError_t batch_enqueue_impl(int, int, int, int, const void*, int, cudaStream_t, long long*);
 // Flattened single-pass batch (batch_single.cuh): size of one member record,
 // filling the record of solver s (s.f as array 0, s.f2 as array 1; tensor
 // maps re-encoded when encode_maps), and enqueueing nsteps launches of the
@@ -135,7 +136,6 @@ cudaError_t sp_member_fill(const Solver& s, void* record, bool encode_maps);
 void sp_member_set_phase(void* record, int phase);
 cudaError_t sp_batch_enqueue(int storage, bool bc, bool fx, const void* members, const void* work, int nwork,
                              int nsteps, cudaStream_t st, long long* launches);
-template <int D> cudaError_t batch_upload_impl(int, const BatchMember*, int, cudaStream_t);
 
 }  // namespace elbm
 

@@ -13,8 +13,7 @@ cudaError_t step_single_impl<2>(const Solver& s, void* dst, long long* launches)
     return step_single_d2q9(s, dst, launches);
 }
 template cudaError_t build_step_graph_impl<2>(const Solver&, int, cudaGraphExec_t*, int*);
-template cudaError_t batch_enqueue_impl<2>(int, int, int, int, cudaStream_t, long long*);
-template cudaError_t batch_upload_impl<2>(int, const BatchMember*, int, cudaStream_t);
+template cudaError_t batch_enqueue_impl<2>(int, int, int, int, const void*, int, cudaStream_t, long long*);
 template cudaError_t init_impl<2>(const Solver&, const void*, const void*, int, long long*);
 template cudaError_t moments_impl<2>(const Solver&, void*, void*, int, long long*);
 template cudaError_t get_populations_impl<2>(const Solver&, void*, int, long long*);

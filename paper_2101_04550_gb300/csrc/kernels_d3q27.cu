@@ -9,8 +9,7 @@ namespace elbm {
 template cudaError_t step_two_pass_impl<3>(const Solver&, int, long long*);
 template cudaError_t step_single_impl<3>(const Solver&, void*, long long*);
 template cudaError_t build_step_graph_impl<3>(const Solver&, int, cudaGraphExec_t*, int*);
-template cudaError_t batch_enqueue_impl<3>(int, int, int, int, cudaStream_t, long long*);
-template cudaError_t batch_upload_impl<3>(int, const BatchMember*, int, cudaStream_t);
+template cudaError_t batch_enqueue_impl<3>(int, int, int, int, const void*, int, cudaStream_t, long long*);
 template cudaError_t init_impl<3>(const Solver&, const void*, const void*, int, long long*);
 template cudaError_t moments_impl<3>(const Solver&, void*, void*, int, long long*);
 template cudaError_t get_populations_impl<3>(const Solver&, void*, int, long long*);

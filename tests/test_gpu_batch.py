@@ -160,6 +160,28 @@ def test_single_pass_batch_every_configuration_bitwise(config):
         assert np.array_equal(s.get_populations(), m.get_populations())
 
 
+@pytest.mark.parametrize("lattice,specs", [(elbm.D3Q27, SPECS3), (elbm.D2Q9, SPECS2)])
+def test_two_pass_batches_live_side_by_side(lattice, specs):
+    """Two two-pass batches of the same lattice and storage mode at once (each
+    keeps its member table in device memory of its own), stepped alternately
+    with different step counts: bit for bit the solo states."""
+    solo = [_make(lattice, sp, elbm.F32_SHIFT, k) for k, sp in enumerate(specs)]
+    mixed = [_make(lattice, sp, elbm.F32_SHIFT, k) for k, sp in enumerate(specs)]
+    half = len(specs) // 2
+    for s in solo[:half]:
+        s.step(9)
+    for s in solo[half:]:
+        s.step(12)
+    with elbm.Batch(mixed[:half]) as b1, elbm.Batch(mixed[half:]) as b2:
+        for k1, k2 in ((3, 5), (6, 7)):
+            b1.step(k1)
+            b2.step(k2)
+    for s, m in zip(solo, mixed):
+        assert np.array_equal(s.get_populations(), m.get_populations())
+    for s in solo + mixed:
+        s.close()
+
+
 def test_single_pass_batches_live_side_by_side():
     """Two single-pass batches of the same storage mode at once (the member
     tables live in each batch's device memory), stepped alternately."""
