@@ -279,7 +279,7 @@ def served_comparison(stream, n_requests, full=False):
     against one-at-a-time plain service on the same GPU.  Every request's
     final velocity in the batched run is compared with its plain run (the
     same kernels, so bit for bit)."""
-    from paper_2101_04550_gb300 import serve
+    from paper_2101_04550_gb300 import elbm, serve
     trace = serve.make_trace(n_requests, rate=20.0, seed=0, steps=2000)
     # warm-up: one small request in both modes (module loading, first graph capture)
     warm = serve.make_trace(4, rate=1000.0, seed=99, steps=20, sizes=(32, 48))
@@ -292,7 +292,7 @@ def served_comparison(stream, n_requests, full=False):
     batched_fifo = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream).run(trace, mode="batched")
     # the same, with the single-pass batches as per-member graphs instead of the flattened launch
     batched_graphs = serve.Server(hbm_budget=8 << 30, chunk_steps=100, stream=stream, policy="srpt",
-                                  sp_config=6).run(trace, mode="batched")
+                                  sp_config=elbm.BATCH_CONFIGS - 1).run(trace, mode="batched")
     srv_plain = serve.Server(stream=stream)
     plain = srv_plain.run(trace, mode="plain")
     plain_two_pass = serve.Server(stream=stream, kernels="two-pass").run(trace, mode="plain")

@@ -241,7 +241,9 @@ long long elbm_launch_count(const elbm_solver* s);
  *    one launch per step of a flattened kernel over a work list of (member,
  *    32 x 16 tile column, z segment) items, with every member's parameter block
  *    and tensor maps in device memory of the batch; the nsteps launches are
- *    captured as a CUDA graph and replayed.  The segment depth (32, 16 or 8
+ *    captured as a CUDA graph and replayed.  The tile shape (32 x 16 columns
+ *    with the TMEM kernel, 32 x 8 with the TMA kernel for periodic, unforced
+ *    members with ny a multiple of 8), the segment depth (32, 16 or 8
  *    planes) and the order of the work list come from an autotuner (see
  *    elbm_batch_tuning), which may also choose per-member graphs: each
  *    member's sequence of solo single-pass launches captured once and replayed
@@ -279,24 +281,32 @@ int elbm_batch_step(elbm_batch* b, int nsteps);
  * so far. */
 int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long long* launches);
 
-/* Single-pass form: the configuration the last elbm_batch_step used for the
- * members the TMEM single pass takes, and the autotuner's timings of two
- * steps of each candidate for the batch's size class (shared by every batch
- * of the process with the same storage mode, walls/force setting and
- * floor(log2(nodes)) of those members):
- *   *config       0..5 the flattened launch (one kernel per step over a work
- *                 list of tile columns of every such member), 6 per-member graphs;
- *   *seg_planes   z planes per work item (32, 16 or 8; 0 for config 6);
+/* Single-pass form: the configuration the last elbm_batch_step used and the
+ * autotuner's timings of two steps of the whole batch in each candidate, for
+ * the batch's tuning key (shared by every batch of the process with the same
+ * storage mode, walls/force setting and floor(log2(nodes)) of its members).
+ * Configurations 0..11 are the flattened launch -- one kernel per step over a
+ * work list of tile columns of every member that kernel takes, the others as
+ * per-member graphs; 12 is per-member graphs for every member:
+ *   *config       0..12;
+ *   *tile_rows    16 (TMEM kernel, configs 0..5), 8 (TMA kernel, configs
+ *                 6..11; periodic, unforced members), 0 for config 12;
+ *   *seg_planes   z planes per work item (32, 16 or 8; 0 for config 12);
  *   *interleaved  1 if the work list interleaves the members item by item,
  *                 0 if it takes them one after another;
- *   ms[7]         tuning times in ms of configs 0..6 (-1 for one not yet timed).
- * Any output pointer may be NULL.  Returns ELBM_OK once the tuning of the
- * size class is complete, 1 while it is still in progress (the tuning spreads
- * over calls with fewer than 14 steps; until it completes config 0 runs),
- * ELBM_ERR_STATE for a two-pass batch or before the first single-pass step. */
-int elbm_batch_tuning(const elbm_batch* b, int* config, int* seg_planes, int* interleaved, double* ms);
+ *   ms[ELBM_BATCH_CONFIGS]  tuning times in ms (-1 for one not yet timed).
+ * Config c has tile_rows 16 for c < 6, 8 for c < 12; seg_planes 32, 16, 8
+ * for c % 3 = 0, 1, 2; interleaved for c % 6 >= 3.  Any output pointer may be
+ * NULL.  Returns ELBM_OK once the tuning of the key is complete (or when no
+ * member takes a flattened kernel, or a configuration is pinned), 1 while it
+ * is still in progress (the tuning spreads over calls with fewer than 26
+ * steps; until it completes config 0 runs), ELBM_ERR_STATE for a two-pass
+ * batch or before the first single-pass step. */
+#define ELBM_BATCH_CONFIGS 13
+int elbm_batch_tuning(const elbm_batch* b, int* config, int* tile_rows, int* seg_planes, int* interleaved,
+                      double* ms);
 
-/* Single-pass form: run configuration `config` (0..6, as elbm_batch_tuning
+/* Single-pass form: run configuration `config` (0..12, as elbm_batch_tuning
  * numbers them) from the next elbm_batch_step on instead of the autotuner's
  * choice; -1 returns to the autotuner.  Every configuration computes the same
  * bits.  ELBM_ERR_ARG for a value out of range, ELBM_ERR_STATE for a

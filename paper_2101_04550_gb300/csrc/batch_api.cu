@@ -85,6 +85,7 @@ struct elbm_batch {
         int nwork = 0;
         bool bc = false;
         bool fx = false;
+        int rows = 16;
     };
     std::map<int, SpGraph> sp_graphs;  // by step count
     struct Staging {                   // pinned host buffer of an asynchronous upload
@@ -129,13 +130,17 @@ constexpr int kGraphsPerMember = 4;  // cached step counts per member
 
 int member_form(const elbm_solver* s) { return elbm::effective_kernel(s) == 3 ? 3 : 1; }
 
-// Autotuner candidates of the single-pass batch: configurations 0..5 are the
-// flattened launch with segments of kSegCand[c % 3] planes, members one after
-// another (c < 3) or interleaved item by item (c >= 3); configuration 6 is
-// per-member graphs.
-constexpr int kSpCandidates = 7;
-constexpr int kSpGraphs = 6;
+// Autotuner candidates of the single-pass batch: configurations 0..11 are
+// the flattened launch -- TMEM kernel on 32 x 16 tile columns (c < 6) or TMA
+// kernel on 32 x 8 (6 <= c < 12), segments of kSegCand[c % 3] planes, members
+// one after another or interleaved item by item ((c % 6) >= 3) -- over the
+// members that kernel takes, the other members as per-member graphs;
+// configuration 12 is per-member graphs for every member.
+constexpr int kSpCandidates = ELBM_BATCH_CONFIGS;
+constexpr int kSpGraphs = ELBM_BATCH_CONFIGS - 1;
 constexpr int kSegCand[3] = {32, 16, 8};
+int cfg_tile_rows(int c) { return c < 6 ? 16 : 8; }
+bool cfg_interleaved(int c) { return (c % 6) >= 3; }
 struct SpTuning {
     double ms[kSpCandidates] = {};
     int next = 0;        // next candidate to time
@@ -282,12 +287,24 @@ cudaError_t run_member_graphs(elbm_batch* b, const std::vector<elbm_solver*>& ms
 cudaError_t join_in(elbm_batch* b);
 cudaError_t join_out(elbm_batch* b);
 
-// Size class of a set of flattened members: floor(log2(total nodes)).
-long long sp_key(const elbm_batch* b, const std::vector<elbm_solver*>& flat)
+// Members the flattened launch of configuration c takes (the others run as
+// per-member graphs).
+std::vector<elbm_solver*> flat_of(const elbm_batch* b, int c, std::vector<elbm_solver*>* rest)
+{
+    std::vector<elbm_solver*> flat;
+    for (auto* s : b->members) {
+        const bool takes = c < 6 ? elbm::single_pass_variant(*s) == 1 : c < kSpGraphs && elbm::sp_tma_member(*s);
+        (takes ? flat : *rest).push_back(s);
+    }
+    return flat;
+}
+
+// Tuning key of a batch: storage, walls/force, floor(log2(total nodes)).
+long long sp_key(const elbm_batch* b, const std::vector<elbm_solver*>& members)
 {
     long long nodes = 0;
     bool bc = false;
-    for (const auto* s : flat) {
+    for (const auto* s : members) {
         nodes += s->N;
         bc = bc || bounded_member(s);
     }
@@ -377,17 +394,17 @@ cudaError_t sp_upload_work(elbm_batch* b, const std::vector<elbm_solver*>& flat,
     std::vector<long long> sig{c};
     for (const auto* s : flat) sig.insert(sig.end(), {s->uid, s->nx, s->ny, s->nz});
     if (sig == b->sp_work_sig && b->sp_work_dev) return cudaSuccess;
-    const int seg = kSegCand[c % 3];
+    const int seg = kSegCand[c % 3], rows = cfg_tile_rows(c);
     std::vector<std::vector<int4>> per(flat.size());
     for (size_t m = 0; m < flat.size(); ++m) {
         const elbm_solver* s = flat[m];
         for (int z0 = 0; z0 < s->nz; z0 += seg)
-            for (int y0 = 0; y0 < s->ny; y0 += 16)
+            for (int y0 = 0; y0 < s->ny; y0 += rows)
                 for (int x0 = 0; x0 < s->nx; x0 += 32)
                     per[m].push_back(make_int4((int)m, x0, y0, z0 | (std::min(s->nz, z0 + seg) << 16)));
     }
     std::vector<int4> work;
-    if (c < 3) {
+    if (!cfg_interleaved(c)) {
         for (auto& v : per) work.insert(work.end(), v.begin(), v.end());
     } else {
         for (size_t k = 0;; ++k) {
@@ -418,10 +435,12 @@ cudaError_t sp_upload_work(elbm_batch* b, const std::vector<elbm_solver*>& flat,
     return staged_upload(b, 1, b->sp_work_dev, work.data(), bytes);
 }
 
-// nsteps steps of the flattened members in configuration c (0..5), as one
+// nsteps steps of the flattened members in configuration c (0..11), as one
 // CUDA graph of nsteps launches (graph = true) or as direct launches.
 cudaError_t run_flat(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c, int nsteps, bool graph)
 {
+    if (flat.empty() || nsteps == 0) return cudaSuccess;
+    const int rows = cfg_tile_rows(c);
     bool bc = false, fx = true;
     for (const auto* s : flat) {
         bc = bc || bounded_member(s);
@@ -432,19 +451,20 @@ cudaError_t run_flat(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c
     if (e == cudaSuccess) e = sp_upload_work(b, flat, c);
     if (e != cudaSuccess) return e;
     if (!graph) {
-        e = elbm::sp_batch_enqueue(b->storage, bc, fx, b->sp_table_dev, b->sp_work_dev, b->sp_nwork, nsteps,
+        e = elbm::sp_batch_enqueue(b->storage, rows, bc, fx, b->sp_table_dev, b->sp_work_dev, b->sp_nwork, nsteps,
                                    b->exec_stream, &b->launches);
     } else {
         elbm_batch::SpGraph& g = b->sp_graphs[nsteps];
-        if (!g.exec || g.nwork != b->sp_nwork || g.bc != bc || g.fx != fx) {
+        if (!g.exec || g.nwork != b->sp_nwork || g.bc != bc || g.fx != fx || g.rows != rows) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
             cudaGraph_t graph_ = nullptr;
             long long dummy = 0;
             e = cudaStreamBeginCapture(b->exec_stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t e1 = elbm::sp_batch_enqueue(b->storage, bc, fx, b->sp_table_dev, b->sp_work_dev,
-                                                              b->sp_nwork, nsteps, b->exec_stream, &dummy);
+                const cudaError_t e1 = elbm::sp_batch_enqueue(b->storage, rows, bc, fx, b->sp_table_dev,
+                                                              b->sp_work_dev, b->sp_nwork, nsteps, b->exec_stream,
+                                                              &dummy);
                 e = cudaStreamEndCapture(b->exec_stream, &graph_);
                 if (e == cudaSuccess) e = e1;
             }
@@ -454,6 +474,7 @@ cudaError_t run_flat(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c
             g.nwork = b->sp_nwork;
             g.bc = bc;
             g.fx = fx;
+            g.rows = rows;
         }
         e = cudaGraphLaunch(g.exec, b->exec_stream);
         if (e == cudaSuccess) b->launches += nsteps;
@@ -463,32 +484,35 @@ cudaError_t run_flat(elbm_batch* b, const std::vector<elbm_solver*>& flat, int c
     return e;
 }
 
-// Time two real steps of every candidate not yet timed for this size class
-// (as many as *steps_left allows); once all are timed the fastest is chosen.
-cudaError_t sp_tune(elbm_batch* b, const std::vector<elbm_solver*>& flat, SpTuning& t, int* steps_left)
+// Time two real steps of the whole batch in every candidate not yet timed
+// for this tuning key (as many as *steps_left allows); once all are timed the
+// fastest is chosen.  Host-side preparation (the uploads of a flattened
+// configuration, the captures of member graphs) stays outside the timed
+// interval.
+cudaError_t sp_tune(elbm_batch* b, SpTuning& t, int* steps_left)
 {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     while (e == cudaSuccess && t.next < kSpCandidates && *steps_left >= 2) {
         const int c = t.next;
-        // host-side preparation outside the timed interval: the uploads of a
-        // flattened configuration, the captures of the member graphs
-        if (c < kSpGraphs) {
+        std::vector<elbm_solver*> rest;
+        const std::vector<elbm_solver*> flat = flat_of(b, c, &rest);
+        if (!flat.empty()) {
             e = join_in(b);
             if (e == cudaSuccess) e = sp_upload_table(b, flat);
             if (e == cudaSuccess) e = sp_upload_work(b, flat, c);
             if (e == cudaSuccess) e = join_out(b);
-        } else {
-            e = ensure_pool(b, std::min((int)flat.size(), kPoolStreams));
-            for (size_t k = 0; k < flat.size() && e == cudaSuccess; ++k) {
-                cudaGraphExec_t exec = nullptr;
-                long long launches = 0;
-                e = member_graph(b, flat[k], 2, b->pool[k % b->pool.size()], &exec, &launches);
-            }
+        }
+        if (e == cudaSuccess && !rest.empty()) e = ensure_pool(b, std::min((int)rest.size(), kPoolStreams));
+        for (size_t k = 0; k < rest.size() && e == cudaSuccess; ++k) {
+            cudaGraphExec_t exec = nullptr;
+            long long launches = 0;
+            e = member_graph(b, rest[k], 2, b->pool[k % b->pool.size()], &exec, &launches);
         }
         if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
-        if (e == cudaSuccess) e = c < kSpGraphs ? run_flat(b, flat, c, 2, false) : run_member_graphs(b, flat, 2);
+        if (e == cudaSuccess) e = run_flat(b, flat, c, 2, false);
+        if (e == cudaSuccess) e = run_member_graphs(b, rest, 2);
         if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
         float ms = 0.f;
@@ -515,35 +539,33 @@ int step_single_form(elbm_batch* b, int nsteps)
         if (member_form(s) != 3 || s->parity != 0 || !s->f2)
             return bfail(ELBM_ERR_STATE, "a member of a single-pass batch no longer steps in the single-pass form");
     reap(b, false);
-    std::vector<elbm_solver*> flat, graphed;
-    for (auto* s : b->members) (elbm::single_pass_variant(*s) == 1 ? flat : graphed).push_back(s);
+    bool any_flat = false;  // does some member take a flattened kernel at all
+    for (const auto* s : b->members)
+        any_flat = any_flat || elbm::single_pass_variant(*s) == 1 || elbm::sp_tma_member(*s);
     cudaError_t e = cudaSuccess;
-    if (!flat.empty()) {
-        const long long key = sp_key(b, flat);
+    int left = nsteps;
+    int c = kSpGraphs;
+    if (any_flat) {
+        const long long key = sp_key(b, b->members);
         SpTuning* t = nullptr;
         {
             std::lock_guard<std::mutex> lock(g_tune_lock);
             t = &g_sp_tuning[key];  // map nodes stay where they are
         }
-        int left = nsteps;
-        // the tuning steps are real steps of the flattened members (an even
-        // number, so each state ends in the array it started in)
-        if (t->chosen < 0 && b->sp_pinned < 0) e = sp_tune(b, flat, *t, &left);
-        // while still tuning: 32-plane segments, member-major
-        const int c = b->sp_pinned >= 0 ? b->sp_pinned : t->chosen >= 0 ? t->chosen : 0;
+        // the tuning steps are real steps of every member (an even number, so
+        // each state ends in the array it started in)
+        if (t->chosen < 0 && b->sp_pinned < 0) e = sp_tune(b, *t, &left);
+        // while still tuning: TMEM tiles, 32-plane segments, member-major
+        c = b->sp_pinned >= 0 ? b->sp_pinned : t->chosen >= 0 ? t->chosen : 0;
         b->sp_key = key;
-        b->sp_config = c;
-        if (e == cudaSuccess && left > 0) {
-            if (c < kSpGraphs) {
-                e = run_flat(b, flat, c, left, true);
-            } else if (left == nsteps) {
-                graphed.insert(graphed.end(), flat.begin(), flat.end());
-            } else {
-                e = run_member_graphs(b, flat, left);
-            }
-        }
     }
-    if (e == cudaSuccess) e = run_member_graphs(b, graphed, nsteps);
+    b->sp_config = c;
+    if (e == cudaSuccess && left > 0) {
+        std::vector<elbm_solver*> rest;
+        const std::vector<elbm_solver*> flat = flat_of(b, c, &rest);
+        e = run_flat(b, flat, c, left, true);
+        if (e == cudaSuccess) e = run_member_graphs(b, rest, left);
+    }
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return bcuda(e, "elbm_batch_step");
@@ -806,16 +828,16 @@ int elbm_batch_info(const elbm_batch* b, int* block_size, double* tuned_ms, long
 int elbm_batch_set_config(elbm_batch* b, int config)
 {
     if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
-    if (config < -1 || config >= kSpCandidates) return bfail(ELBM_ERR_ARG, "config must be -1 or 0..6");
+    if (config < -1 || config >= kSpCandidates) return bfail(ELBM_ERR_ARG, "config must be -1 or 0..12");
     if (b->form != 3) return bfail(ELBM_ERR_STATE, "only single-pass batches have a configuration");
     b->sp_pinned = config;
     return ELBM_OK;
 }
 
-int elbm_batch_tuning(const elbm_batch* b, int* config, int* seg_planes, int* interleaved, double* ms)
+int elbm_batch_tuning(const elbm_batch* b, int* config, int* tile_rows, int* seg_planes, int* interleaved, double* ms)
 {
     if (!b) return bfail(ELBM_ERR_ARG, "batch is NULL");
-    if (b->form != 3 || b->sp_key < 0) return bfail(ELBM_ERR_STATE, "no single-pass batch step has run");
+    if (b->form != 3 || b->sp_config < 0) return bfail(ELBM_ERR_STATE, "no single-pass batch step has run");
     SpTuning t;
     {
         std::lock_guard<std::mutex> lock(g_tune_lock);
@@ -824,11 +846,14 @@ int elbm_batch_tuning(const elbm_batch* b, int* config, int* seg_planes, int* in
     }
     const int c = b->sp_config;
     if (config) *config = c;
+    if (tile_rows) *tile_rows = c < kSpGraphs ? cfg_tile_rows(c) : 0;
     if (seg_planes) *seg_planes = c < kSpGraphs ? kSegCand[c % 3] : 0;
-    if (interleaved) *interleaved = c < kSpGraphs ? (c >= 3 ? 1 : 0) : 0;
+    if (interleaved) *interleaved = c < kSpGraphs && cfg_interleaved(c) ? 1 : 0;
     if (ms)
         for (int k = 0; k < kSpCandidates; ++k) ms[k] = k < t.next ? t.ms[k] : -1.0;
-    return t.chosen >= 0 ? ELBM_OK : 1;
+    // no member takes a flattened kernel: nothing to tune, per-member graphs
+    if (b->sp_key < 0) return ELBM_OK;
+    return t.chosen >= 0 || b->sp_pinned >= 0 ? ELBM_OK : 1;
 }
 
 void elbm_batch_destroy(elbm_batch* b)

@@ -128,14 +128,16 @@ template <int D>
 cudaError_t batch_enqueue_impl(int, int, int, int, const void*, int, cudaStream_t, long long*);
 // Flattened single-pass batch (batch_single.cuh): size of one member record,
 // filling the record of solver s (s.f as array 0, s.f2 as array 1; tensor
-// maps re-encoded when encode_maps), and enqueueing nsteps launches of the
-// batch kernel over a work list of nwork items (x member, y x0, z y0,
-// w z0 | z1 << 16) in device memory.
+// maps re-encoded when encode_maps), and enqueueing nsteps launches of a
+// batch kernel (TMEM kernel on 32 x 16 tile columns or TMA kernel on 32 x 8)
+// over a work list of nwork items (x member, y x0, z y0, w z0 | z1 << 16) in
+// device memory; sp_tma_member: whether the 32 x 8 form takes a solver.
 size_t sp_member_bytes();
 cudaError_t sp_member_fill(const Solver& s, void* record, bool encode_maps);
 void sp_member_set_phase(void* record, int phase);
-cudaError_t sp_batch_enqueue(int storage, bool bc, bool fx, const void* members, const void* work, int nwork,
-                             int nsteps, cudaStream_t st, long long* launches);
+cudaError_t sp_batch_enqueue(int storage, int tile_y, bool bc, bool fx, const void* members, const void* work,
+                             int nwork, int nsteps, cudaStream_t st, long long* launches);
+bool sp_tma_member(const Solver& s);
 
 }  // namespace elbm
 

@@ -208,15 +208,18 @@ struct TmaLayout {
     static_assert(tile_bytes % 128 == 0, "tile boxes must keep 128-byte alignment");
 };
 
+// One tile column of a single-pass step: the 32 x 8 columns at (x0, y0),
+// planes z0 .. z1-1, from p.f into dst; every thread of the block takes part.
+// tm_tile / tm_row are the tensor maps (8-row tile box) of p.f, kernel
+// parameters or device memory made visible to the tensor-map proxy.
 template <int ST>
-__global__ void __launch_bounds__(kTmaThreads, 2)
-    k_single_pass_tma(const __grid_constant__ CUtensorMap tm_tile, const __grid_constant__ CUtensorMap tm_row,
-                      StepParams p, void* dst)
+__device__ __forceinline__ void tma_tile_step(const CUtensorMap* tm_tile, const CUtensorMap* tm_row,
+                                              const StepParams& p, void* dst, int x0, int y0, int z0, int z1,
+                                              unsigned char* smem_raw)
 {
     using S = Storage<ST>;
     using T = typename S::T;
     using L = TmaLayout<ST>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     const uint32_t sbase = (raw_addr + 127u) & ~127u;
     unsigned char* base = smem_raw + (sbase - raw_addr);
@@ -228,9 +231,6 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     auto qready = [&](int s) { return bar0 + 8u * (10 + s); };
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L::off_abort);
 
-    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-    const int z0 = blockIdx.z * kSegPlanes;
-    const int z1 = min(p.nz, z0 + kSegPlanes);
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             const int zk = plane_of(k);
             if (lane == 0) {
                 mbar_arrive_expect_tx(full_t(b), L::tile_bytes);
-                tma_load_4d(sbase + L::off_tile + b * L::tile_bytes, &tm_tile, x0, y0, zk, 0, full_t(b));
+                tma_load_4d(sbase + L::off_tile + b * L::tile_bytes, tm_tile, x0, y0, zk, 0, full_t(b));
                 mbar_arrive_expect_tx(full_r(r), 2 * L::row_box_bytes);
-                tma_load_4d(sbase + L::off_rows + (2 * r) * L::row_stride, &tm_row, x0, ylo, zk, 0, full_r(r));
-                tma_load_4d(sbase + L::off_rows + (2 * r + 1) * L::row_stride, &tm_row, x0, yhi, zk, 0, full_r(r));
+                tma_load_4d(sbase + L::off_rows + (2 * r) * L::row_stride, tm_row, x0, ylo, zk, 0, full_r(r));
+                tma_load_4d(sbase + L::off_rows + (2 * r + 1) * L::row_stride, tm_row, x0, yhi, zk, 0, full_r(r));
             }
             unsigned* cols = reinterpret_cast<unsigned*>(base + L::off_cols + r * L::cols_bytes);
             for (int c = lane; c < 27 * 2 * kTileY; c += 32) {
@@ -377,6 +377,19 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         qz_prev = qz_cur;
         qz_cur = qz_next;
     }
+}
+
+// The single-pass step of one grid on 32 x 8 tiles: block (bx, by, bz) takes
+// the tile column at (32 bx, 8 by), planes kSegPlanes bz onwards.
+template <int ST>
+__global__ void __launch_bounds__(kTmaThreads, 2)
+    k_single_pass_tma(const __grid_constant__ CUtensorMap tm_tile, const __grid_constant__ CUtensorMap tm_row,
+                      const __grid_constant__ StepParams p, void* dst)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int z0 = blockIdx.z * kSegPlanes;
+    tma_tile_step<ST>(&tm_tile, &tm_row, p, dst, blockIdx.x * kTileX, blockIdx.y * kTileY, z0,
+                      min(p.nz, z0 + kSegPlanes), smem_raw);
 }
 
 // TMA needs 16-byte aligned rows and whole tiles: nx a multiple of 32, ny a

@@ -22,6 +22,7 @@ OPT_EQUILIBRIUM, OPT_KERNEL, OPT_RHO_REF = 1, 2, 3
 OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z, OPT_WALLS_Y = 4, 5, 6, 7
 OPT_U_REF_X, OPT_U_REF_Y, OPT_U_REF_Z, OPT_U_REF_AUTO = 8, 9, 10, 11
 NRED = 13
+BATCH_CONFIGS = 13   # single-pass batch configurations (ELBM_BATCH_CONFIGS)
 ERRORS = {0: "OK", -1: "ARG", -2: "UNREALIZABLE", -3: "OOM", -4: "CUDA", -5: "NONFINITE",
           -6: "TIMEOUT", -7: "STATE"}
 STORAGE_NAMES = {"f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT, "f32s": F32_SHIFT}
@@ -87,7 +88,7 @@ def load(build_if_missing: bool = True):
         L.elbm_kernel_form.argtypes = [vp, ctypes.POINTER(ip)]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
         L.elbm_batch_tuning.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip),
-                                         ctypes.POINTER(dp)]
+                                         ctypes.POINTER(ip), ctypes.POINTER(dp)]
         L.elbm_batch_set_config.argtypes = [vp, ip]
         L.elbm_batch_add.argtypes = [vp, vp]
         L.elbm_batch_remove.argtypes = [vp, vp]
@@ -325,20 +326,23 @@ class Batch:
         return {"block_size": bs.value, "tuned_ms": {128: ms[0], 256: ms[1]}, "launches": launches.value}
 
     def set_config(self, config):
-        """Single-pass batches: pin the configuration (0..5 flattened launch,
-        6 per-member graphs) or return to the autotuner (-1)."""
+        """Single-pass batches: pin the configuration (0..11 flattened launch,
+        12 per-member graphs; see elbm_batch_tuning) or return to the
+        autotuner (-1)."""
         _check(load().elbm_batch_set_config(self._h, int(config)))
 
     def tuning(self):
         """Single-pass batches: the configuration of the last step and the
         autotuner's two-step timings (ms, -1 for a candidate not yet timed)."""
-        c, seg, inter = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        ms = (ctypes.c_double * 7)()
-        rc = load().elbm_batch_tuning(self._h, ctypes.byref(c), ctypes.byref(seg), ctypes.byref(inter), ms)
+        c, rows, seg, inter = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * BATCH_CONFIGS)()
+        rc = load().elbm_batch_tuning(self._h, ctypes.byref(c), ctypes.byref(rows), ctypes.byref(seg),
+                                      ctypes.byref(inter), ms)
         if rc < 0:
             _check(rc)
-        return {"config": c.value, "seg_planes": seg.value, "interleaved": bool(inter.value),
-                "member_graphs": c.value == 6, "tuned": rc == 0, "ms": list(ms)}
+        return {"config": c.value, "tile_rows": rows.value, "seg_planes": seg.value,
+                "interleaved": bool(inter.value), "member_graphs": c.value == BATCH_CONFIGS - 1,
+                "tuned": rc == 0, "ms": list(ms)}
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -141,7 +141,7 @@ class Server:
                       two-pass form for the rest; "two-pass": the two-pass form
                       for every request
     sp_config         configuration of the single-pass batches (None: the
-                      library's autotuner; 0..5 the flattened launch, 6
+                      library's autotuner; 0..11 the flattened launch, 12
                       per-member graphs -- see elbm_batch_set_config)
     clock             callable giving seconds (wall clock by default)
     """

@@ -133,14 +133,15 @@ def test_single_pass_batch_matches_solo_bitwise(storage):
         assert np.array_equal(s.get_populations(), m.get_populations())
 
 
-@pytest.mark.parametrize("config", range(7))
+@pytest.mark.parametrize("config", range(elbm.BATCH_CONFIGS))
 def test_single_pass_batch_every_configuration_bitwise(config):
-    """Each configuration of the single-pass batch -- the flattened launch
-    with 32-, 16- or 8-plane segments, members one after another or
-    interleaved, and per-member graphs -- pinned, over odd and even step
-    counts, with a member whose grid the TMEM kernel does not take (32 x 8
-    TMA tiles, always per-member graphs) beside them: bit for bit the solo
-    states; the flattened configurations make one launch per step."""
+    """Each configuration of the single-pass batch -- the flattened launch on
+    32 x 16 (TMEM) or 32 x 8 (TMA) tile columns with 32-, 16- or 8-plane
+    segments, members one after another or interleaved, and per-member
+    graphs -- pinned, over odd and even step counts, with a member whose grid
+    only the 32 x 8 kernel takes beside them (per-member graphs under the
+    TMEM configurations): bit for bit the solo states; a flattened
+    configuration makes one launch per step."""
     specs = SPECS_SP + [((32, 8, 16), (1.0, 1.0, 1.0), 0.4, 0.02)]
     solo = [_make_sp(sp, elbm.F16_SHIFT, k) for k, sp in enumerate(specs)]
     mixed = [_make_sp(sp, elbm.F16_SHIFT, k) for k, sp in enumerate(specs)]
@@ -153,9 +154,16 @@ def test_single_pass_batch_every_configuration_bitwise(config):
         b.step(5)
         b.step(11)
         launches = b.info()["launches"] - before
-        assert b.tuning()["config"] == config
-    flat_launches = 16 if config < 6 else 16 * len(SPECS_SP)
-    assert launches == flat_launches + 16  # + the TMA member's own launches
+        t = b.tuning()
+    assert t["config"] == config and t["tuned"]
+    assert t["tile_rows"] == (16 if config < 6 else 8 if config < 12 else 0)
+    if config < 6:
+        want = 16 + 16          # one launch per step + the 32 x 8 member's own launches
+    elif config < 12:
+        want = 16               # every member in the 32 x 8 flattened launch
+    else:
+        want = 16 * len(specs)  # per-member graphs
+    assert launches == want
     for s, m in zip(solo, mixed):
         assert np.array_equal(s.get_populations(), m.get_populations())
 
