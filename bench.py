@@ -49,8 +49,9 @@ CHANNEL = dict(workload="D3Q27 turbulent channel 512x128x256, lam=(2,1,2), walls
 CHANNEL.update(nu=CHANNEL["u_tau"] * 64 / 180.0, g=CHANNEL["u_tau"] ** 2 / 64)
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0
-KERNEL_NAMES = {0: "automatic", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass"}
-KERNEL_LAUNCHES = {1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range", 3: "k_single_pass_tmem"}
+KERNEL_NAMES = {0: "automatic", 1: "two-pass", 2: "graph-pipelined", 3: "single-pass", 4: "fused-in-place"}
+KERNEL_LAUNCHES = {1: "k_anomaly+k_collide", 2: "k_anomaly_range+k_collide_range", 3: "k_single_pass_tmem",
+                   4: "k_fused_aa"}
 # ncu DRAM bytes (read + write) of one step of the timed kernel form, keyed by
 # the hash of the kernel sources they were measured on, the storage and the form
 # (the form as it ran: 0, automatic, ran the two-pass form before that choice
@@ -392,9 +393,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32s", choices=["f32", "f32s", "f16", "bf16"])
-    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="0 automatic (the library's default: single pass where it applies), 1 two-pass in place, "
-                         "2 graph-pipelined in place, 3 single pass (two arrays)")
+                         "2 graph-pipelined in place, 3 single pass (two arrays), 4 fused in place")
     ap.add_argument("--reduce-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle leg (and with it the accuracy check that uses its result)")
@@ -530,7 +531,9 @@ def main():
     variants = {}
     var_steps = max(50, min(args.steps, 200))
     D3_VARIANTS = (("f32_shift_two_pass", elbm.F32_SHIFT, 1), ("f32_shift_graph_pipelined", elbm.F32_SHIFT, 2),
-                   ("f16_shift_single_pass", elbm.F16_SHIFT, 3), ("f16_shift_two_pass", elbm.F16_SHIFT, 1))
+                   ("f32_shift_fused_in_place", elbm.F32_SHIFT, 4),
+                   ("f16_shift_single_pass", elbm.F16_SHIFT, 3), ("f16_shift_two_pass", elbm.F16_SHIFT, 1),
+                   ("f16_shift_fused_in_place", elbm.F16_SHIFT, 4))
     if not args.no_variants and rank == 0:
         for name, st, ker in D3_VARIANTS:
             sv, tot, sts, _, _ = timed_run(st, ker, var_steps, args.reduce_every)

@@ -78,13 +78,24 @@ extern "C" {
  *       unforced D2Q9 grids, for which elbm_create (or setting this option)
  *       allocates the second population array -- twice the population
  *       memory; if that allocation fails the solver keeps one array and steps
- *       in the two-pass form.  Other D3Q27 grids, D2Q9 with walls or a force,
- *       and the second-order equilibrium: the two-pass form.
+ *       in the fused in-place form (4) where it applies, else the two-pass
+ *       form.  Other D3Q27 grids: form 4 where it applies; D2Q9 with walls or
+ *       a force, the second-order equilibrium and the rest: the two-pass form.
  *       elbm_kernel_form() reports the choice;
  *   1 = two-pass, in place: an anomaly pass over the grid, then the collide pass;
  *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide
  *       kernels, so that the collide kernels re-read populations from L2;
  *       forms 1 and 2 release a second population array if one is held;
+ *   4 = fused in place (D3Q27; periodic, unforced, extended or product-form
+ *       equilibrium): one array in the AA layout, one cooperative launch per
+ *       step in which a block owns a 32 x 8 tile column, keeps each node's
+ *       populations in registers from its anomaly to its collision one plane
+ *       later, and exchanges the anomaly with the neighbouring tile columns
+ *       through the anomaly field and progress counters (bounded waits), so
+ *       every population is read once.  Needs every tile column resident at
+ *       once (at most two per SM); other grids, walls, force and the
+ *       second-order equilibrium take the two-pass form.  Releases a second
+ *       array if one is held;
  *   3 = single pass with a second population array: every block recomputes
  *       the anomaly around its tile and reads the populations once.  D3Q27:
  *       TMA-fed with the populations parked in tensor memory when nx is a
@@ -206,7 +217,8 @@ int elbm_mode_sums(elbm_solver* s, const double* k, const double* dir, double* o
 int elbm_sync(elbm_solver* s);
 
 /* Kernel form the next elbm_step of s uses: 1 two-pass, 2 graph-pipelined,
- * 3 single pass (ELBM_OPT_KERNEL and the grid decide it; see there), or
+ * 3 single pass, 4 fused in place (ELBM_OPT_KERNEL and the grid decide it;
+ * see there), or
  * ELBM_ERR_ARG for NULL.  For form 3, *variant (if not NULL) receives the
  * single-pass kernel: 1 TMEM (32 x 16 tiles), 2 TMA (32 x 8 tiles),
  * 3 cp.async-staged (D3Q27), 4 the D2Q9 row march; 0 for the other forms.

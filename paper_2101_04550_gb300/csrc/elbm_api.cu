@@ -134,7 +134,7 @@ void fill_params(const Solver& s, StepParams& p)
 // Kernel form a step uses.  Automatic (0): once the second population array
 // has been allocated, the single pass on the D3Q27 grids its TMEM kernel takes
 // (x a multiple of 32 nodes, y of 16) and on periodic, unforced D2Q9 grids;
-// the two-pass form otherwise.  The second-order equilibrium runs in the
+// else the fused in-place form where it applies, the two-pass form otherwise.  The second-order equilibrium runs in the
 // two-pass form; walls and the body force in the two-pass form or, on the
 // TMEM geometry of D3Q27, the TMEM single pass (the D2Q9 single pass has
 // neither).
@@ -149,10 +149,18 @@ bool auto_single(const Solver* s)
     return s->D == 3 ? elbm::single_tmem_geometry(*s) : !bounded_solver(s);
 }
 
+// The fused in-place form takes D3Q27 grids whose tile columns all fit the
+// GPU at once, periodic and unforced, with the extended or product-form equilibrium.
+static bool fused_applies(const Solver* s) { return s->fused_ok && !bounded_solver(s) && s->eq_mode != 2; }
+
 int effective_kernel(const Solver* s)
 {
     if (s->eq_mode == 2) return 1;
-    if (s->kernel == 0) return (s->f2 && auto_single(s)) ? 3 : 1;
+    if (s->kernel == 0) {
+        if (s->f2 && auto_single(s)) return 3;
+        return fused_applies(s) ? 4 : 1;
+    }
+    if (s->kernel == 4) return fused_applies(s) ? 4 : 1;
     if (!bounded_solver(s)) return s->kernel;
     return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;
 }
@@ -200,10 +208,10 @@ size_t population_bytes(const elbm_solver* s)
 // explicitly (kernel 3), a failed allocation is an error; for the automatic
 // form (kernel 0) on a grid the TMEM single pass takes it is an attempt, and
 // without the array the solver steps in the two-pass form.  The in-place forms
-// (1, 2) release it: the current state always sits in s->f.
+// (1, 2, 4) release it: the current state always sits in s->f.
 int ensure_second_array(elbm_solver* s, int kernel)
 {
-    if (kernel == 1 || kernel == 2) {
+    if (kernel == 1 || kernel == 2 || kernel == 4) {
         if (s->f2) {
             cudaFreeAsync(s->f2, s->stream);  // stream-ordered: after the queued steps that use it
             s->f2 = nullptr;
@@ -289,6 +297,8 @@ int elbm_create(int lattice, int nx, int ny, int nz, const double* stretch, doub
         return rc;
     }
     s->bytes = population_bytes(s) + qbytes;
+    s->fused_ok = elbm::fused_available(*s) ? 1 : 0;
+    (void)cudaGetLastError();  // an occupancy query that failed only means "no fused form"
     const int rc = ensure_second_array(s, s->kernel);
     if (rc != ELBM_OK) {
         elbm_destroy(s);
@@ -304,7 +314,7 @@ void elbm_destroy(elbm_solver* s)
     drop_graphs(s);
     // stream-ordered frees: they wait for the solver's queued work, not the device
     for (void* ptr : {s->f, s->f2, (void*)s->q, (void*)s->status, (void*)s->mom, (void*)s->partials,
-                      (void*)s->red_out})
+                      (void*)s->red_out, (void*)s->progress})
         if (ptr) cudaFreeAsync(ptr, s->stream);
     delete s;
 }
@@ -321,8 +331,8 @@ int elbm_set_option(elbm_solver* s, int key, double value)
             s->eq_mode = (int)value;
             return ELBM_OK;
         case ELBM_OPT_KERNEL: {
-            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2 or 3");
+            if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0 && value != 4.0)
+                return fail(ELBM_ERR_ARG, "kernel must be 0, 1, 2, 3 or 4");
             const int rc = ensure_second_array(s, (int)value);
             if (rc != ELBM_OK) return rc;
             s->kernel = (int)value;
@@ -446,6 +456,22 @@ int elbm_step(elbm_solver* s, int n)
             e = (s->D == 2) ? elbm::step_single_impl<2>(*s, s->f2, &s->launches)
                             : elbm::step_single_impl<3>(*s, s->f2, &s->launches);
             std::swap(s->f, s->f2);
+            --left;
+        } else if (kernel == 4) {
+            // fused in place: one cooperative launch per step, progress counters on first use
+            if (!s->progress) {
+                const int nblocks = ((s->nx + 31) / 32) * ((s->ny + 7) / 8);
+                e = cudaMallocAsync((void**)&s->progress, sizeof(unsigned long long) * nblocks, s->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemsetAsync(s->progress, 0, sizeof(unsigned long long) * nblocks, s->stream);
+                if (e != cudaSuccess) {
+                    s->progress = nullptr;
+                    break;
+                }
+                s->bytes += sizeof(unsigned long long) * nblocks;
+            }
+            e = elbm::step_fused_impl(*s, s->parity, s->progress, ++s->epoch, &s->launches);
+            s->parity ^= 1;
             --left;
         } else if (kernel == 2) {
             if (!s->graph_exec[s->parity]) {

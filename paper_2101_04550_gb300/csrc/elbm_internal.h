@@ -56,7 +56,10 @@ struct Solver {
     double u_ref[3] = {0, 0, 0};   // storage baseline velocity U0 (shifted storage modes)
     int u_ref_auto = 0;            // 1: U0 = mean velocity of the field given to elbm_init
     int eq_mode = 0;
-    int kernel = 0;       // 0 auto, 1 two-pass, 2 graph-pipelined, 3 single pass (two arrays)
+    int kernel = 0;       // 0 auto, 1 two-pass, 2 graph-pipelined, 3 single pass (two arrays), 4 fused in place
+    int fused_ok = 0;     // the fused in-place form fits this grid (every tile column co-resident)
+    unsigned long long* progress = nullptr;  // fused form: per-block progress counters
+    unsigned long long epoch = 0;            // fused form: launches so far
     int walls_y = 0;
     int parity = 0;
     int initialised = 0;
@@ -110,8 +113,11 @@ template <int D> cudaError_t step_bounded_impl(const Solver&, int, long long*);
 template <int D> cudaError_t step_single_impl(const Solver&, void*, long long*);
 template <> cudaError_t step_single_impl<2>(const Solver&, void*, long long*);  // kernels_d2q9.cu
 bool single_tmem_geometry(const Solver& s);
+bool fused_available(const Solver& s);
+cudaError_t step_fused_impl(const Solver& s, int parity, unsigned long long* progress, unsigned long long epoch,
+                            long long* launches);
 int single_pass_variant(const Solver& s);
-// Kernel form a step of s uses (1 two-pass, 2 graph-pipelined, 3 single pass):
+// Kernel form a step of s uses (1 two-pass, 2 graph-pipelined, 3 single pass, 4 fused in place):
 // the requested form where it applies, else the two-pass form.
 int effective_kernel(const Solver* s);
 // Whether the automatic form steps s in the single pass (given its second array).

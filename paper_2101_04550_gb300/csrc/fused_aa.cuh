@@ -1,0 +1,177 @@
+// Fused in-place step (one population array, AA pattern) of the D3Q27
+// lattice: each population is read from memory once per step.
+//
+// The two-pass form reads every node's populations twice -- once for the
+// anomaly Q~ (Eq. Deviation) of the whole grid, once more to collide --
+// because the central difference of Eq. Paastar1 needs the anomaly of the face
+// neighbours at the same time level.  Here a block owns a 32 x 8 tile column
+// and marches along z; a thread keeps its node's populations of plane z in
+// registers from the moment it gathers them (as part of computing the
+// anomaly of plane z) until it collides plane z one iteration later:
+//   iteration z:  gather plane z+1 (AA read slots), moments, anomaly; write
+//                 Q~_xxx, Q~_yyy of plane z+1 to the anomaly field (Q~_zzz
+//                 stays in registers); publish "planes 0..z+1 done";
+//                 wait until the four face-neighbouring tile columns have
+//                 published plane z; collide plane z (Eqs. Paastar1, 27eqext,
+//                 LBGK) with the populations gathered one iteration earlier
+//                 and scatter to the AA write slots.
+// The z difference of plane 0 needs Q~_zzz of plane nz-1, which a prologue
+// computes first (from the same, still untouched slots).
+//
+// Why blocks cannot race on populations: in the AA pattern a node reads and
+// writes one slot set and the slot sets of distinct nodes are disjoint, so a
+// block only ever touches the slot sets of its own nodes.  The one value that
+// crosses blocks is the anomaly: its writer publishes a per-block progress
+// counter with release semantics after the block's writes, the reader
+// acquires its neighbours' counters before reading.  The counters grow
+// monotonically over launches (epoch * (nz + 2) + planes done), so they
+// never need resetting.  All blocks of a launch are co-resident (cooperative
+// launch); every wait is bounded in time and, when it gives up, sets
+// ELBM_ERR_TIMEOUT in the status word and stops the block.
+//
+// The per-node arithmetic is the two-pass form's (gather, moments, anomaly,
+// relax_streamed, scatter through the AA slots), so the results agree bit for
+// bit.
+#pragma once
+#include "single_pass_tma.cuh"
+
+namespace elbm {
+
+constexpr int kFuTileX = 32, kFuTileY = 8;
+constexpr int kFuThreads = kFuTileX * kFuTileY;
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int ST, int PAR>
+__global__ void __launch_bounds__(kFuThreads, 2)
+    k_fused_aa(const __grid_constant__ StepParams p, unsigned long long* progress, unsigned long long epoch)
+{
+    constexpr int D = 3;
+    const int tx = threadIdx.x % kFuTileX, ty = threadIdx.x / kFuTileX;
+    const int gx = blockIdx.x * kFuTileX + tx, gy = blockIdx.y * kFuTileY + ty;
+    const bool active = gx < p.nx && gy < p.ny;
+    const int bx = blockIdx.x, by = blockIdx.y, nbx = gridDim.x, nby = gridDim.y;
+    const unsigned long long base = epoch * (unsigned long long)(p.nz + 2);
+    // the four face-neighbouring tile columns (periodic)
+    const int nb[4] = {by * nbx + (bx == 0 ? nbx - 1 : bx - 1), by * nbx + (bx == nbx - 1 ? 0 : bx + 1),
+                       (by == 0 ? nby - 1 : by - 1) * nbx + bx, (by == nby - 1 ? 0 : by + 1) * nbx + bx};
+    const int me = by * nbx + bx;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+
+    float* qx = p.q;
+    float* qy = p.q + p.N;
+    // node (gx, gy, z); inactive threads of a ragged tile take a valid node and do nothing with it
+    auto node_at = [&](int z) { return make_node<D>(p, (active ? gx + gy * p.nx : 0) + z * p.plane); };
+
+    // Q~_zzz of plane nz-1 (the z difference of plane 0 wraps around)
+    float qz_prev = 0.f;
+    if (active) {
+        float g[27];
+        gather<D, ST, PAR>(p, node_at(p.nz - 1), g);
+        float drho, j[3];
+        moments<D>(p, g, drho, j);
+        qz_prev = anomaly(p, 2, j[2], j[2] * (1.0f / (p.rho_ref + drho)));
+    }
+    // plane 0: populations kept for its collision, anomaly published
+    float gc[27], mc_drho = 0.f, mc_j[3] = {0.f, 0.f, 0.f}, qz_cur = 0.f;
+    {
+        const Node n0 = node_at(0);
+        if (active) {
+            gather<D, ST, PAR>(p, n0, gc);
+            moments<D>(p, gc, mc_drho, mc_j);
+            const float inv = 1.0f / (p.rho_ref + mc_drho);
+            qx[n0.cell] = anomaly(p, 0, mc_j[0], mc_j[0] * inv);
+            qy[n0.cell] = anomaly(p, 1, mc_j[1], mc_j[1] * inv);
+            qz_cur = anomaly(p, 2, mc_j[2], mc_j[2] * inv);
+        }
+    }
+    for (int z = 0; z < p.nz; ++z) {
+        // ------------------------------------------- anomaly of plane z+1
+        float gn[27], mn_drho = 0.f, mn_j[3] = {0.f, 0.f, 0.f}, qz_next = 0.f;
+        {
+            const int zn = z + 1 == p.nz ? 0 : z + 1;
+            const Node nn = node_at(zn);
+            if (active) {
+                gather<D, ST, PAR>(p, nn, gn);
+                moments<D>(p, gn, mn_drho, mn_j);
+                const float inv = 1.0f / (p.rho_ref + mn_drho);
+                if (z + 1 < p.nz) {
+                    qx[nn.cell] = anomaly(p, 0, mn_j[0], mn_j[0] * inv);
+                    qy[nn.cell] = anomaly(p, 1, mn_j[1], mn_j[1] * inv);
+                }
+                qz_next = anomaly(p, 2, mn_j[2], mn_j[2] * inv);
+            }
+        }
+        // --------------------------------- publish, wait for the neighbours
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_u64(progress + me, base + (unsigned long long)min(z + 2, p.nz));
+            const unsigned long long need = base + (unsigned long long)(z + 1);
+            const unsigned long long t0 = globaltimer_ns();
+            for (int k = 0; k < 4 && !s_abort; ++k) {
+                for (unsigned it = 0; ld_acquire_u64(progress + nb[k]) < need; ++it) {
+                    if ((it & 63) == 63 && globaltimer_ns() - t0 > kTmaWaitNs) {
+                        atomicExch(p.status, ELBM_ERR_TIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) return;
+        // --------------------------------------------------- collide plane z
+        if (active) {
+            const Node n = node_at(z);
+            float d[3] = {0.f, 0.f, 0.f};
+            if (p.eq_mode == 0) {
+                d[0] = (__ldcg(qx + n.at(1, 0, 0)) - __ldcg(qx + n.at(-1, 0, 0))) * p.inv_2lam[0];
+                d[1] = (__ldcg(qy + n.at(0, 1, 0)) - __ldcg(qy + n.at(0, -1, 0))) * p.inv_2lam[1];
+                d[2] = (qz_next - qz_prev) * p.inv_2lam[2];
+            }
+            using S = Storage<ST>;
+            typename S::T* f = static_cast<typename S::T*>(p.f);
+            const int cell_o = opaque(n.cell);
+            auto put = [&](int i, float v) {
+                const int slot = (PAR == 0) ? (26 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
+                S::store(f + slot, S::shifted ? v : fmaf(p.bw[i], p.rho_ref, v));
+            };
+            relax_streamed<D>(p, [&](int i) { return gc[i]; }, put, mc_drho, mc_j, d);
+        }
+        qz_prev = qz_cur;
+        qz_cur = qz_next;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) gc[i] = gn[i];
+        mc_drho = mn_drho;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) mc_j[a] = mn_j[a];
+    }
+}
+
+// Whether the fused form takes solver s and how many of its blocks fit the GPU at once.
+template <int ST>
+bool fused_fits(const Solver& s, int* blocks_x, int* blocks_y)
+{
+    *blocks_x = (s.nx + kFuTileX - 1) / kFuTileX;
+    *blocks_y = (s.ny + kFuTileY - 1) / kFuTileY;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_aa<ST, 0>, kFuThreads, 0) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return (long long)per_sm * s.num_sms >= (long long)*blocks_x * *blocks_y;
+}
+
+}  // namespace elbm

@@ -24,6 +24,7 @@
 // edge take the periodic image of their position: they supply the anomaly of
 // the wrapped node and relax nothing.
 #pragma once
+#include <utility>
 #include "step_kernels.cuh"
 
 namespace elbm {
@@ -73,6 +74,37 @@ __device__ __forceinline__ unsigned stage_node(const StepParams& p, int cell, un
         cp_async4(col + i * stride, stage_src<ST>(p, idx));
     }
     return halves;
+}
+
+// Programmatic dependent launch.  A kernel launched after this one with the
+// programmatic-serialization attribute may be scheduled once every block of
+// this one has signalled (pdl_release, at the top of the kernel); its blocks
+// run their prologue and then stop in pdl_wait until this kernel has finished
+// and its memory operations are visible.  Without the attribute pdl_wait
+// returns at once.
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kernel` with the programmatic-serialization attribute (outside a
+// stream capture; inside one, as an ordinary launch).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }

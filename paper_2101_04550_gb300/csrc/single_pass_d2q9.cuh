@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kD2Threads) k_single_pass_d2q9(const __grid_co
     using S = Storage<ST>;
     using T = typename S::T;
     __shared__ float qxs[3][kD2Threads];
+    pdl_release();
     const int t = threadIdx.x;
     const int xr = blockIdx.x * kD2Cols - 1 + t;  // column before the periodic wrap
     const bool inner = t >= 1 && t <= kD2Cols && xr < p.nx;
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(kD2Threads) k_single_pass_d2q9(const __grid_co
     // raw populations of row k, loaded one row ahead so that the loads of row
     // k + 1 are in flight while row k - 1 is relaxed
     T raw[9];
+    pdl_wait();  // the previous step has written the source array
     {
         const int node = wrapi(y0 - 1, p.ny) * p.nx + gx;
 #pragma unroll
@@ -119,9 +121,10 @@ inline cudaError_t step_single_d2q9(const Solver& s, void* dst, long long* launc
     p.parity = 0;
     const int seg = d2q9_segment_rows(s);
     const dim3 grid((unsigned)((s.nx + kD2Cols - 1) / kD2Cols), (unsigned)((s.ny + seg - 1) / seg));
-    ELBM_DISPATCH_STORAGE(s.storage, { k_single_pass_d2q9<ST><<<grid, kD2Threads, 0, s.stream>>>(p, dst, seg); });
-    ++*launches;
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ELBM_DISPATCH_STORAGE(s.storage, { e = launch_pdl(k_single_pass_d2q9<ST>, grid, dim3(kD2Threads), 0, s.stream, p, dst, seg); });
+    if (e == cudaSuccess) ++*launches;
+    return e;
 }
 
 }  // namespace elbm

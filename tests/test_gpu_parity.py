@@ -143,7 +143,7 @@ def test_d3q27_half_storage_turbulence(storage):
 
 
 # ----------------------------------------------------------- D3Q27 cases
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 def test_d3q27_turbulence_ragged_stretched(kernel):
     """Seeded solenoidal field on a ragged 37x20x23 grid, lam = (1, 1.5, 2), T = 0.5."""
     n, lam = (37, 20, 23), (1.0, 1.5, 2.0)
@@ -180,9 +180,9 @@ def test_d3q27_minimum_grid():
                                        (elbm.D2Q9, (300, 700)), (elbm.D2Q9, (33, 5))])
 @pytest.mark.parametrize("storage", [elbm.F32, elbm.F16_SHIFT, elbm.F32_SHIFT, elbm.BF16_SHIFT])
 def test_kernel_forms_agree_bitwise(lattice, n, storage):
-    """The two-pass, graph-pipelined and (D3Q27) single-pass forms evaluate the same
-    per-node arithmetic, so the states agree bit for bit, across launches of
-    several steps and both streaming parities."""
+    """The two-pass, graph-pipelined, single-pass and (D3Q27) fused in-place
+    forms evaluate the same per-node arithmetic, so the states agree bit for
+    bit, across launches of several steps and both streaming parities."""
     D = 2 if lattice == elbm.D2Q9 else 3
     if D == 3:
         rho, u = inputs.isotropic_turbulence(n, seed=2, k0=3.0, u_rms=0.05)
@@ -190,7 +190,7 @@ def test_kernel_forms_agree_bitwise(lattice, n, storage):
         rho, u = inputs.double_shear_layer(n, U=0.1)
     lam = (1.0, 2.0, 1.0)
     outs = []
-    for kernel in (1, 2, 3):
+    for kernel in ((1, 2, 3, 4) if D == 3 else (1, 2, 3)):
         with elbm.Solver(lattice, n, stretch=lam, T=0.5, nu=0.01, storage=storage, kernel=kernel) as s:
             s.init(rho, u)
             for k in (1, 2, 4):

@@ -98,6 +98,23 @@ def test_tmem_single_pass_1000_steps_periodic(storage):
 
 
 @pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT, elbm.F16_SHIFT])
+def test_fused_in_place_1000_steps_periodic(storage):
+    """The fused in-place form (one array, AA pattern, one cooperative launch
+    per step) on the same wave over 1000 steps against the oracle, launched in
+    pieces of odd and even length (both AA parities between launches)."""
+    c = PERIODIC
+    rho, u = periodic_field()
+    with elbm.Solver(elbm.D3Q27, c["n"], stretch=c["lam"], T=c["T"], nu=c["nu"], storage=storage, kernel=4,
+                     u_ref="mean" if storage == elbm.F16_SHIFT else None) as s:
+        assert s.kernel_form == (4, 0)
+        s.init(rho, u)
+        for k in (1, 7, 100, STEPS - 108):
+            s.step(k)
+        _, ug = s.moments()
+    check(ug, oracle_result("periodic"), storage)
+
+
+@pytest.mark.parametrize("storage", [elbm.F32, elbm.F32_SHIFT, elbm.F16_SHIFT])
 def test_tmem_single_pass_1000_steps_walls_and_force(storage):
     """Channel lattice lam = (2, 1, 2), T = 0.55, half-way bounce-back walls in
     y and a body force along x (Sec. III.E), 1000 steps of the TMEM single pass
@@ -128,6 +145,10 @@ def test_tmem_single_pass_1000_steps_walls_and_force(storage):
     (elbm.D3Q27, (37, 20, 23), {"kernel": 3}, (3, 3)),            # requested: cp.async-staged
     (elbm.D3Q27, (37, 20, 23), {"kernel": 3, "walls_y": True}, (1, 0)),
     (elbm.D3Q27, (64, 32, 32), {"kernel": 2}, (2, 0)),
+    (elbm.D3Q27, (48, 40, 36), {"kernel": 4}, (4, 0)),            # fused in place, ragged tiles
+    (elbm.D3Q27, (64, 32, 32), {"kernel": 4, "walls_y": True}, (1, 0)),
+    (elbm.D3Q27, (64, 32, 32), {"kernel": 4, "equilibrium": 2}, (1, 0)),
+    (elbm.D2Q9, (64, 64), {"kernel": 4}, (1, 0)),
 ])
 def test_automatic_kernel_form(lattice, n, opts, want):
     """ELBM_OPT_KERNEL = 0 (the default) takes the TMEM single pass where its
