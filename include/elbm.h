@@ -376,6 +376,15 @@ int elbm_step_noalloc(int lattice, int nx, int ny, int nz, const double* stretch
  */
 int elbm_selftest_wait_timeout(int limit_ms, void* stream);
 
+/*
+ * The same self-test for the other bounded wait of the library: the fused
+ * in-place form (ELBM_OPT_KERNEL 4) waits for progress counters of the
+ * neighbouring tile columns.  This call runs that wait on a counter that
+ * nothing advances, with a bound of limit_ms (1..2000) milliseconds, and
+ * returns as elbm_selftest_wait_timeout does (ELBM_ERR_TIMEOUT expected).
+ */
+int elbm_selftest_counter_timeout(int limit_ms, void* stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* elbm_last_error(void);
 

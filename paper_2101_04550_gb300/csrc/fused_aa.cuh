@@ -16,7 +16,9 @@
 //                 LBGK) with the populations gathered one iteration earlier
 //                 and scatter to the AA write slots.
 // The z difference of plane 0 needs Q~_zzz of plane nz-1, which a prologue
-// computes first (from the same, still untouched slots).
+// computes first (from the same, still untouched slots); the z difference of
+// plane nz-1 needs Q~_zzz of plane 0, kept from before plane 0 was collided
+// (its slots hold the next time level by then).
 //
 // Why blocks cannot race on populations: in the AA pattern a node reads and
 // writes one slot set and the slot sets of distinct nodes are disjoint, so a
@@ -49,6 +51,22 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Wait until *counter >= need (acquire), bounded: gives up once
+// globaltimer - t0 exceeds limit_ns, then stores ELBM_ERR_TIMEOUT in *status
+// and returns false.
+__device__ __forceinline__ bool bounded_progress_wait(const unsigned long long* counter, unsigned long long need,
+                                                      int* status, unsigned long long t0,
+                                                      unsigned long long limit_ns)
+{
+    for (unsigned it = 0; ld_acquire_u64(counter) < need; ++it) {
+        if ((it & 63) == 63 && globaltimer_ns() - t0 > limit_ns) {
+            atomicExch(status, ELBM_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
 }
 
 template <int ST, int PAR>
@@ -96,20 +114,18 @@ __global__ void __launch_bounds__(kFuThreads, 2)
             qz_cur = anomaly(p, 2, mc_j[2], mc_j[2] * inv);
         }
     }
+    const float qz_first = qz_cur;  // Q~_zzz of plane 0 before plane 0 is collided
     for (int z = 0; z < p.nz; ++z) {
         // ------------------------------------------- anomaly of plane z+1
-        float gn[27], mn_drho = 0.f, mn_j[3] = {0.f, 0.f, 0.f}, qz_next = 0.f;
-        {
-            const int zn = z + 1 == p.nz ? 0 : z + 1;
-            const Node nn = node_at(zn);
+        float gn[27], mn_drho = 0.f, mn_j[3] = {0.f, 0.f, 0.f}, qz_next = qz_first;
+        if (z + 1 < p.nz) {
+            const Node nn = node_at(z + 1);
             if (active) {
                 gather<D, ST, PAR>(p, nn, gn);
                 moments<D>(p, gn, mn_drho, mn_j);
                 const float inv = 1.0f / (p.rho_ref + mn_drho);
-                if (z + 1 < p.nz) {
-                    qx[nn.cell] = anomaly(p, 0, mn_j[0], mn_j[0] * inv);
-                    qy[nn.cell] = anomaly(p, 1, mn_j[1], mn_j[1] * inv);
-                }
+                qx[nn.cell] = anomaly(p, 0, mn_j[0], mn_j[0] * inv);
+                qy[nn.cell] = anomaly(p, 1, mn_j[1], mn_j[1] * inv);
                 qz_next = anomaly(p, 2, mn_j[2], mn_j[2] * inv);
             }
         }
@@ -120,15 +136,8 @@ __global__ void __launch_bounds__(kFuThreads, 2)
             st_release_u64(progress + me, base + (unsigned long long)min(z + 2, p.nz));
             const unsigned long long need = base + (unsigned long long)(z + 1);
             const unsigned long long t0 = globaltimer_ns();
-            for (int k = 0; k < 4 && !s_abort; ++k) {
-                for (unsigned it = 0; ld_acquire_u64(progress + nb[k]) < need; ++it) {
-                    if ((it & 63) == 63 && globaltimer_ns() - t0 > kTmaWaitNs) {
-                        atomicExch(p.status, ELBM_ERR_TIMEOUT);
-                        s_abort = 1;
-                        break;
-                    }
-                }
-            }
+            for (int k = 0; k < 4 && !s_abort; ++k)
+                if (!bounded_progress_wait(progress + nb[k], need, p.status, t0, kTmaWaitNs)) s_abort = 1;
         }
         __syncthreads();
         if (s_abort) return;
@@ -152,11 +161,13 @@ __global__ void __launch_bounds__(kFuThreads, 2)
         }
         qz_prev = qz_cur;
         qz_cur = qz_next;
+        if (z + 1 < p.nz) {
 #pragma unroll
-        for (int i = 0; i < 27; ++i) gc[i] = gn[i];
-        mc_drho = mn_drho;
+            for (int i = 0; i < 27; ++i) gc[i] = gn[i];
+            mc_drho = mn_drho;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) mc_j[a] = mn_j[a];
+            for (int a = 0; a < 3; ++a) mc_j[a] = mn_j[a];
+        }
     }
 }
 

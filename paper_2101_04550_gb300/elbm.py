@@ -38,7 +38,7 @@ EXPORTS = ["elbm_create", "elbm_destroy", "elbm_set_option", "elbm_init", "elbm_
            "elbm_last_error", "elbm_batch_create", "elbm_batch_step", "elbm_batch_info", "elbm_batch_destroy",
            "elbm_batch_add", "elbm_batch_remove", "elbm_batch_size",
            "elbm_step_noalloc", "elbm_selftest_wait_timeout", "elbm_mode_sums", "elbm_kernel_form",
-           "elbm_batch_tuning", "elbm_batch_set_config"]
+           "elbm_batch_tuning", "elbm_batch_set_config", "elbm_selftest_counter_timeout"]
 
 
 class ElbmError(RuntimeError):
@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
         L.elbm_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
         L.elbm_batch_step.argtypes = [vp, ip]
         L.elbm_selftest_wait_timeout.argtypes = [ip, vp]
+        L.elbm_selftest_counter_timeout.argtypes = [ip, vp]
         L.elbm_mode_sums.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)]
         L.elbm_kernel_form.argtypes = [vp, ctypes.POINTER(ip)]
         L.elbm_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_longlong)]
@@ -368,11 +369,14 @@ def _addr(b):
     return b
 
 
-def selftest_wait_timeout(limit_ms=50, stream=None):
-    """Run the library's bounded device-side wait on a barrier that never
-    completes; returns the error code (ELBM_ERR_TIMEOUT, -6, when it gave up
-    as designed) and the library's message."""
+def selftest_wait_timeout(limit_ms=50, stream=None, counter=False):
+    """Run one of the library's bounded device-side waits on something that
+    never happens -- an mbarrier phase (the TMA-fed kernels' wait) or, with
+    counter=True, a progress counter (the fused in-place form's wait);
+    returns the error code (ELBM_ERR_TIMEOUT, -6, when it gave up as
+    designed) and the library's message."""
     L = load()
     sp = None if stream is None else ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
-    rc = L.elbm_selftest_wait_timeout(int(limit_ms), sp)
+    fn = L.elbm_selftest_counter_timeout if counter else L.elbm_selftest_wait_timeout
+    rc = fn(int(limit_ms), sp)
     return rc, L.elbm_last_error().decode()
