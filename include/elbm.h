@@ -78,9 +78,8 @@ extern "C" {
  *       unforced D2Q9 grids, for which elbm_create (or setting this option)
  *       allocates the second population array -- twice the population
  *       memory; if that allocation fails the solver keeps one array and steps
- *       in the fused in-place form (4) where it applies, else the two-pass
- *       form.  Other D3Q27 grids: form 4 where it applies; D2Q9 with walls or
- *       a force, the second-order equilibrium and the rest: the two-pass form.
+ *       in the two-pass form.  Other D3Q27 grids, D2Q9 with walls or a force,
+ *       and the second-order equilibrium: the two-pass form.
  *       elbm_kernel_form() reports the choice;
  *   1 = two-pass, in place: an anomaly pass over the grid, then the collide pass;
  *   2 = graph-pipelined, in place: a CUDA graph of per-chunk anomaly and collide

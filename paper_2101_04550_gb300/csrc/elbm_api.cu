@@ -134,7 +134,8 @@ void fill_params(const Solver& s, StepParams& p)
 // Kernel form a step uses.  Automatic (0): once the second population array
 // has been allocated, the single pass on the D3Q27 grids its TMEM kernel takes
 // (x a multiple of 32 nodes, y of 16) and on periodic, unforced D2Q9 grids;
-// else the fused in-place form where it applies, the two-pass form otherwise.  The second-order equilibrium runs in the
+// the two-pass form otherwise (the fused in-place form, 4, reads less but
+// runs slower, so only a request for it selects it).  The second-order equilibrium runs in the
 // two-pass form; walls and the body force in the two-pass form or, on the
 // TMEM geometry of D3Q27, the TMEM single pass (the D2Q9 single pass has
 // neither).
@@ -156,10 +157,7 @@ static bool fused_applies(const Solver* s) { return s->fused_ok && !bounded_solv
 int effective_kernel(const Solver* s)
 {
     if (s->eq_mode == 2) return 1;
-    if (s->kernel == 0) {
-        if (s->f2 && auto_single(s)) return 3;
-        return fused_applies(s) ? 4 : 1;
-    }
+    if (s->kernel == 0) return (s->f2 && auto_single(s)) ? 3 : 1;
     if (s->kernel == 4) return fused_applies(s) ? 4 : 1;
     if (!bounded_solver(s)) return s->kernel;
     return (s->kernel == 3 && elbm::single_tmem_geometry(*s)) ? 3 : 1;

@@ -135,9 +135,8 @@ def test_tmem_single_pass_1000_steps_walls_and_force(storage):
     (elbm.D3Q27, (64, 32, 32), {}, (3, 1)),                       # TMEM geometry: single pass
     (elbm.D3Q27, (64, 32, 32), {"walls_y": True, "force": (1e-6, 0, 0)}, (3, 1)),
     (elbm.D3Q27, (64, 32, 32), {"equilibrium": 2}, (1, 0)),       # second order: two-pass only
-    (elbm.D3Q27, (48, 48, 48), {}, (4, 0)),                       # x not a multiple of 32: fused in place
-    (elbm.D3Q27, (32, 8, 16), {}, (4, 0)),                        # y not a multiple of 16: fused in place
-    (elbm.D3Q27, (48, 48, 48), {"walls_y": True}, (1, 0)),        # walls: two-pass
+    (elbm.D3Q27, (48, 48, 48), {}, (1, 0)),                       # x not a multiple of 32
+    (elbm.D3Q27, (32, 8, 16), {}, (1, 0)),                        # y not a multiple of 16
     (elbm.D2Q9, (64, 64), {}, (3, 4)),                             # D2Q9: the row-march single pass
     (elbm.D2Q9, (33, 5), {}, (3, 4)),
     (elbm.D2Q9, (64, 64), {"walls_y": True}, (1, 0)),             # walls: two-pass (no D2Q9 single pass)
@@ -153,8 +152,8 @@ def test_tmem_single_pass_1000_steps_walls_and_force(storage):
 ])
 def test_automatic_kernel_form(lattice, n, opts, want):
     """ELBM_OPT_KERNEL = 0 (the default) takes the TMEM single pass where its
-    geometry holds, the fused in-place form on the other periodic D3Q27 grids
-    and the two-pass form elsewhere; the form reported is the one the step runs."""
+    geometry holds and the two-pass form elsewhere (the fused in-place form
+    only when asked for); the form reported is the one the step runs."""
     with elbm.Solver(lattice, n, T=1 / 3, nu=0.02, storage=elbm.F32_SHIFT, **opts) as s:
         assert s.kernel_form == want
 
