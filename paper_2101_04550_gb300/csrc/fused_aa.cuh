@@ -1,20 +1,20 @@
 // Fused in-place step (one population array, AA pattern) of the D3Q27
-// lattice: each population is read from memory once per step.
+// lattice: one launch per step, each population read from DRAM once.
 //
 // The two-pass form reads every node's populations twice -- once for the
 // anomaly Q~ (Eq. Deviation) of the whole grid, once more to collide --
 // because the central difference of Eq. Paastar1 needs the anomaly of the face
 // neighbours at the same time level.  Here a block owns a 32 x 8 tile column
-// and marches along z; a thread keeps its node's populations of plane z in
-// registers from the moment it gathers them (as part of computing the
-// anomaly of plane z) until it collides plane z one iteration later:
-//   iteration z:  gather plane z+1 (AA read slots), moments, anomaly; write
-//                 Q~_xxx, Q~_yyy of plane z+1 to the anomaly field (Q~_zzz
-//                 stays in registers); publish "planes 0..z+1 done";
-//                 wait until the four face-neighbouring tile columns have
-//                 published plane z; collide plane z (Eqs. Paastar1, 27eqext,
-//                 LBGK) with the populations gathered one iteration earlier
-//                 and scatter to the AA write slots.
+// and marches along z with the anomaly kFuLookahead (L) planes ahead of the
+// collision:
+//   iteration z:  gather plane z+L (AA read slots), moments, anomaly; write
+//                 Q~_xxx, Q~_yyy of plane z+L to the anomaly field (Q~_zzz
+//                 goes to a ring of registers); publish "planes 0..z+L
+//                 done"; wait until the four face-neighbouring tile columns
+//                 have published plane z (done L iterations earlier, so the
+//                 wait rarely blocks); gather plane z again -- read L planes
+//                 ago, so mostly from L2 -- and collide it (Eqs. Paastar1,
+//                 27eqext, LBGK), scattering to the AA write slots.
 // The z difference of plane 0 needs Q~_zzz of plane nz-1, which a prologue
 // computes first (from the same, still untouched slots); the z difference of
 // plane nz-1 needs Q~_zzz of plane 0, kept from before plane 0 was collided
@@ -69,11 +69,14 @@ __device__ __forceinline__ bool bounded_progress_wait(const unsigned long long* 
     return true;
 }
 
+// Planes the anomaly runs ahead of the collision.
+constexpr int kFuLookahead = 2;
+
 template <int ST, int PAR>
-__global__ void __launch_bounds__(kFuThreads, 2)
+__global__ void __launch_bounds__(kFuThreads, 3)
     k_fused_aa(const __grid_constant__ StepParams p, unsigned long long* progress, unsigned long long epoch)
 {
-    constexpr int D = 3;
+    constexpr int D = 3, LA = kFuLookahead;
     const int tx = threadIdx.x % kFuTileX, ty = threadIdx.x / kFuTileX;
     const int gx = blockIdx.x * kFuTileX + tx, gy = blockIdx.y * kFuTileY + ty;
     const bool active = gx < p.nx && gy < p.ny;
@@ -91,49 +94,42 @@ __global__ void __launch_bounds__(kFuThreads, 2)
     float* qy = p.q + p.N;
     // node (gx, gy, z); inactive threads of a ragged tile take a valid node and do nothing with it
     auto node_at = [&](int z) { return make_node<D>(p, (active ? gx + gy * p.nx : 0) + z * p.plane); };
-
-    // Q~_zzz of plane nz-1 (the z difference of plane 0 wraps around)
-    float qz_prev = 0.f;
-    if (active) {
-        float g[27];
-        gather<D, ST, PAR>(p, node_at(p.nz - 1), g);
-        float drho, j[3];
+    // anomaly of the node at plane z: Q~_xxx, Q~_yyy to the field, Q~_zzz returned
+    auto anomaly_plane = [&](int z, bool publish_xy) {
+        const Node n = node_at(z);
+        float g[27], drho, j[3];
+        gather<D, ST, PAR>(p, n, g);
         moments<D>(p, g, drho, j);
-        qz_prev = anomaly(p, 2, j[2], j[2] * (1.0f / (p.rho_ref + drho)));
-    }
-    // plane 0: populations kept for its collision, anomaly published
-    float gc[27], mc_drho = 0.f, mc_j[3] = {0.f, 0.f, 0.f}, qz_cur = 0.f;
-    {
-        const Node n0 = node_at(0);
-        if (active) {
-            gather<D, ST, PAR>(p, n0, gc);
-            moments<D>(p, gc, mc_drho, mc_j);
-            const float inv = 1.0f / (p.rho_ref + mc_drho);
-            qx[n0.cell] = anomaly(p, 0, mc_j[0], mc_j[0] * inv);
-            qy[n0.cell] = anomaly(p, 1, mc_j[1], mc_j[1] * inv);
-            qz_cur = anomaly(p, 2, mc_j[2], mc_j[2] * inv);
+        const float inv = 1.0f / (p.rho_ref + drho);
+        if (publish_xy) {
+            qx[n.cell] = anomaly(p, 0, j[0], j[0] * inv);
+            qy[n.cell] = anomaly(p, 1, j[1], j[1] * inv);
         }
+        return anomaly(p, 2, j[2], j[2] * inv);
+    };
+    // ring[k]: Q~_zzz of the own node at plane z - 1 + k, k = 0 .. LA + 1
+    float ring[LA + 2];
+#pragma unroll
+    for (int k = 0; k < LA + 2; ++k) ring[k] = 0.f;
+    float qz_first = 0.f;
+    if (active) {
+        ring[0] = anomaly_plane(p.nz - 1, false);  // plane -1, periodic
+#pragma unroll
+        for (int k = 0; k < LA; ++k)
+            if (k < p.nz) ring[k + 1] = anomaly_plane(k, true);
+        qz_first = ring[1];  // plane 0, before it is collided
     }
-    const float qz_first = qz_cur;  // Q~_zzz of plane 0 before plane 0 is collided
     for (int z = 0; z < p.nz; ++z) {
-        // ------------------------------------------- anomaly of plane z+1
-        float gn[27], mn_drho = 0.f, mn_j[3] = {0.f, 0.f, 0.f}, qz_next = qz_first;
-        if (z + 1 < p.nz) {
-            const Node nn = node_at(z + 1);
-            if (active) {
-                gather<D, ST, PAR>(p, nn, gn);
-                moments<D>(p, gn, mn_drho, mn_j);
-                const float inv = 1.0f / (p.rho_ref + mn_drho);
-                qx[nn.cell] = anomaly(p, 0, mn_j[0], mn_j[0] * inv);
-                qy[nn.cell] = anomaly(p, 1, mn_j[1], mn_j[1] * inv);
-                qz_next = anomaly(p, 2, mn_j[2], mn_j[2] * inv);
-            }
-        }
+        // ------------------------------------------ anomaly of plane z + LA
+        const int za = z + LA;
+        float qa = za == p.nz ? qz_first : 0.f;
+        if (active && za < p.nz) qa = anomaly_plane(za, true);
+        ring[LA + 1] = qa;
         // --------------------------------- publish, wait for the neighbours
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release_u64(progress + me, base + (unsigned long long)min(z + 2, p.nz));
+            st_release_u64(progress + me, base + (unsigned long long)min(za + 1, p.nz));
             const unsigned long long need = base + (unsigned long long)(z + 1);
             const unsigned long long t0 = globaltimer_ns();
             for (int k = 0; k < 4 && !s_abort; ++k)
@@ -141,14 +137,17 @@ __global__ void __launch_bounds__(kFuThreads, 2)
         }
         __syncthreads();
         if (s_abort) return;
-        // --------------------------------------------------- collide plane z
+        // ---------------------------- collide plane z (gathered once more)
         if (active) {
             const Node n = node_at(z);
+            float g[27], drho, j[3];
+            gather<D, ST, PAR>(p, n, g);
+            moments<D>(p, g, drho, j);
             float d[3] = {0.f, 0.f, 0.f};
             if (p.eq_mode == 0) {
                 d[0] = (__ldcg(qx + n.at(1, 0, 0)) - __ldcg(qx + n.at(-1, 0, 0))) * p.inv_2lam[0];
                 d[1] = (__ldcg(qy + n.at(0, 1, 0)) - __ldcg(qy + n.at(0, -1, 0))) * p.inv_2lam[1];
-                d[2] = (qz_next - qz_prev) * p.inv_2lam[2];
+                d[2] = (ring[2] - ring[0]) * p.inv_2lam[2];
             }
             using S = Storage<ST>;
             typename S::T* f = static_cast<typename S::T*>(p.f);
@@ -157,17 +156,10 @@ __global__ void __launch_bounds__(kFuThreads, 2)
                 const int slot = (PAR == 0) ? (26 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
                 S::store(f + slot, S::shifted ? v : fmaf(p.bw[i], p.rho_ref, v));
             };
-            relax_streamed<D>(p, [&](int i) { return gc[i]; }, put, mc_drho, mc_j, d);
+            relax_streamed<D>(p, [&](int i) { return g[i]; }, put, drho, j, d);
         }
-        qz_prev = qz_cur;
-        qz_cur = qz_next;
-        if (z + 1 < p.nz) {
 #pragma unroll
-            for (int i = 0; i < 27; ++i) gc[i] = gn[i];
-            mc_drho = mn_drho;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) mc_j[a] = mn_j[a];
-        }
+        for (int k = 0; k < LA + 1; ++k) ring[k] = ring[k + 1];
     }
 }
 
