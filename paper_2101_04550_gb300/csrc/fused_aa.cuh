@@ -126,14 +126,15 @@ __global__ void __launch_bounds__(kFuThreads, 3)
         if (active && za < p.nz) qa = anomaly_plane(za, true);
         ring[LA + 1] = qa;
         // --------------------------------- publish, wait for the neighbours
+        // (the release store after the block barrier orders every thread's
+        // anomaly writes before the counter; lanes 0..3 of warp 0 then wait
+        // on the four neighbours side by side)
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release_u64(progress + me, base + (unsigned long long)min(za + 1, p.nz));
+        if (threadIdx.x == 0) st_release_u64(progress + me, base + (unsigned long long)min(za + 1, p.nz));
+        if (threadIdx.x < 4) {
             const unsigned long long need = base + (unsigned long long)(z + 1);
-            const unsigned long long t0 = globaltimer_ns();
-            for (int k = 0; k < 4 && !s_abort; ++k)
-                if (!bounded_progress_wait(progress + nb[k], need, p.status, t0, kTmaWaitNs)) s_abort = 1;
+            if (!bounded_progress_wait(progress + nb[threadIdx.x], need, p.status, globaltimer_ns(), kTmaWaitNs))
+                s_abort = 1;
         }
         __syncthreads();
         if (s_abort) return;
