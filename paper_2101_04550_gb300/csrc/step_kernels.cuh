@@ -452,8 +452,29 @@ __device__ __forceinline__ void block_reduce(double* acc, double* out)
     }
 }
 
-// Stage 2: per-block FP64 partial sums (grid-stride over nodes); vorticity and
-// d_x u_x by central differences with node spacing lam.  With walls the
+// Compensated FP32 sum: hi + lo carries the running sum to about twice FP32's
+// precision -- each addition is split exactly into its rounded sum and the
+// rounding error (Knuth's TwoSum error-free transformation), and the errors
+// accumulate in lo.  For the few dozen terms a thread adds, hi + lo is within
+// about n 2^-48 of the exact sum, so per-thread partial sums keep FP64-grade
+// accuracy while the arithmetic stays on the FP32 pipes (FP64 issue is far
+// slower on this GPU); the sums across threads and blocks are FP64.
+struct Sum2f {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float err = (hi - (s - bp)) + (x - bp);
+        hi = s;
+        lo += err;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Stage 2: per-block FP64 partial sums (grid-stride over nodes, compensated
+// FP32 within a thread); vorticity and d_x u_x by central differences with
+// node spacing lam.  With walls the
 // velocity beyond a wall is the negated value of the wall-adjacent node
 // (no slip half-way between the nodes), and the wall-normal gradient of u_x
 // at each wall node comes from the quadratic through the wall (u = 0, a
@@ -461,11 +482,9 @@ __device__ __forceinline__ void block_reduce(double* acc, double* out)
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* mom, double* partials)
 {
-    double acc[ELBM_NRED];
-#pragma unroll
-    for (int k = 0; k < ELBM_NRED; ++k) acc[k] = 0.0;
-    acc[9] = DBL_MAX;
-    acc[11] = 0.0;
+    Sum2f sum[ELBM_NRED];  // entries 9 (min) and 11 (max) unused
+    float fmin_ = FLT_MAX, umax = 0.f;
+    int nonfinite = 0;
     const float* ux = mom + p.N;
     const float* uy = mom + 2 * (size_t)p.N;
     const float* uz = mom + 3 * (size_t)p.N;
@@ -487,7 +506,7 @@ __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* m
         float w2 = (dxuy - dyux) * (dxuy - dyux);
         if (walls && (n.ylo || n.yhi)) {
             const float second = n.ylo ? ux[n.at(0, 1, 0)] : ux[n.at(0, -1, 0)];
-            acc[12] += (double)((9.0f * u0 - second) * (1.0f / (3.0f * p.lam[1])));
+            sum[12].add((9.0f * u0 - second) * (1.0f / (3.0f * p.lam[1])));
         }
         if (D == 3) {
             const float dyuz = dy(uz);
@@ -497,19 +516,25 @@ __global__ void __launch_bounds__(kBlock) k_red_sum(StepParams p, const float* m
             w2 += (dyuz - dzuy) * (dyuz - dzuy) + (dzux - dxuz) * (dzux - dxuz);
         }
         const float dxux = (ux[n.at(1, 0, 0)] - ux[n.at(-1, 0, 0)]) * ix;
-        acc[0] += (double)r;
-        acc[1] += (double)(r * u0);
-        acc[2] += (double)(r * u1);
-        acc[3] += (double)(r * u2);
-        acc[4] += (double)(r * uu);
-        acc[5] += (double)uu;
-        acc[6] += (double)w2;
-        acc[7] += (double)(dxux * dxux);
-        acc[8] += (double)(u0 * u0);
-        acc[9] = fmin(acc[9], (double)mom[4 * (size_t)p.N + cell]);
-        acc[10] += finite ? 0.0 : 1.0;
-        acc[11] = fmax(acc[11], finite ? (double)sqrtf(uu) : 0.0);
+        sum[0].add(r);
+        sum[1].add(r * u0);
+        sum[2].add(r * u1);
+        sum[3].add(r * u2);
+        sum[4].add(r * uu);
+        sum[5].add(uu);
+        sum[6].add(w2);
+        sum[7].add(dxux * dxux);
+        sum[8].add(u0 * u0);
+        fmin_ = fminf(fmin_, mom[4 * (size_t)p.N + cell]);
+        nonfinite += finite ? 0 : 1;
+        umax = fmaxf(umax, finite ? sqrtf(uu) : 0.f);
     }
+    double acc[ELBM_NRED];
+#pragma unroll
+    for (int k = 0; k < ELBM_NRED; ++k) acc[k] = sum[k].value();
+    acc[9] = fmin_ == FLT_MAX ? DBL_MAX : (double)fmin_;
+    acc[10] = (double)nonfinite;
+    acc[11] = (double)umax;
     block_reduce(acc, partials + (size_t)blockIdx.x * ELBM_NRED);
 }
 

@@ -247,3 +247,33 @@ def test_single_pass_batch_membership_and_bounded_members():
     for s, m in zip(solo, mixed):
         assert m.steps_done == s.steps_done
         assert np.array_equal(s.get_populations(), m.get_populations())
+
+
+def test_d2q9_single_pass_members_batch_bitwise():
+    """D2Q9 solvers in the automatic form (the row-march single pass) batch
+    together as per-member graphs: bit for bit the solo states, over an odd
+    and an even step count (the arrays swap)."""
+    specs = [((256, 128, 1), (1.0, 1.0, 1.0), 0.5, 0.01), ((300, 77, 1), (1.0, 2.0, 1.0), 0.5, 0.02),
+             ((64, 64, 1), (2.0, 1.0, 1.0), 1 / 3, 0.02)]
+
+    def make(spec, seed):
+        n, lam, T, nu = spec
+        s = elbm.Solver(elbm.D2Q9, n, stretch=lam, T=T, nu=nu, storage=elbm.F32_SHIFT,
+                        stream=torch.cuda.current_stream())
+        s.init(*_fields(n, seed, 2))
+        return s
+
+    solo = [make(sp, k) for k, sp in enumerate(specs)]
+    mixed = [make(sp, k) for k, sp in enumerate(specs)]
+    assert all(m.kernel_form == (3, 4) for m in mixed)
+    for s in solo:
+        s.step(12)
+    with elbm.Batch(mixed) as b:
+        b.step(5)
+        b.step(7)
+        assert b.tuning()["member_graphs"]
+    for s, m in zip(solo, mixed):
+        assert m.steps_done == 12
+        assert np.array_equal(s.get_populations(), m.get_populations())
+    for s in solo + mixed:
+        s.close()
