@@ -280,9 +280,15 @@ __device__ __forceinline__ void moments(const StepParams& p, const float* g, flo
 
 // Diagonal anomaly Q~_aaa = rho u_a (lam_a^2 - 3T) - rho u_a^3 = j_a (lam_a^2 - 3T - u_a^2)
 // (Eq. Deviation, R = 1).
+//
+// Rounding steps here and in the equilibrium below are spelled out (fmaf
+// where a product and a sum are fused, __fmul_rn / __fadd_rn / __fsub_rn
+// where they are not), so that the compiler has no contraction left to
+// choose: every kernel form computes the same roundings, whatever the code
+// around the helpers, and the forms agree bit for bit by construction.
 __device__ __forceinline__ float anomaly(const StepParams& p, int a, float ja, float ua)
 {
-    return ja * (p.lam2m3T[a] - ua * ua);
+    return __fmul_rn(ja, fmaf(-ua, ua, p.lam2m3T[a]));
 }
 
 // ------------------------------------------------- extended equilibrium + BGK
@@ -303,32 +309,32 @@ __device__ __forceinline__ void for_each_equilibrium(const StepParams& p, float 
     float A[3][3], dl[3][3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float s = dP[a] * p.inv_lam2[a];
-        const float t = du[a] * p.inv_lam[a];
-        dl[a][0] = 0.5f * (s - t);
+        const float s = __fmul_rn(dP[a], p.inv_lam2[a]);
+        const float t = __fmul_rn(du[a], p.inv_lam[a]);
+        dl[a][0] = __fmul_rn(0.5f, __fsub_rn(s, t));
         dl[a][1] = -s;
-        dl[a][2] = 0.5f * (s + t);
+        dl[a][2] = __fmul_rn(0.5f, __fadd_rn(s, t));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) A[a][c] = p.base[a][c] + dl[a][c];
+        for (int c = 0; c < 3; ++c) A[a][c] = __fadd_rn(p.base[a][c], dl[a][c]);
     }
     // rho_ref is folded into the x factors: dlx_r = rho_ref delta_x, base_xr = rho_ref base_x
     float dlx_r[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dlx_r[c] = p.rho_ref * dl[0][c];
+    for (int c = 0; c < 3; ++c) dlx_r[c] = __fmul_rn(p.rho_ref, dl[0][c]);
 #pragma unroll
     for (int cy = 0; cy < 3; ++cy) {
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
-            const float pxy = A[0][cx] * A[1][cy];
+            const float pxy = __fmul_rn(A[0][cx], A[1][cy]);
             // rho_ref (prod_{x,y} Psi - prod_{x,y} base)
-            const float dxy_r = fmaf(dlx_r[cx], A[1][cy], p.base_xr[cx] * dl[1][cy]);
+            const float dxy_r = fmaf(dlx_r[cx], A[1][cy], __fmul_rn(p.base_xr[cx], dl[1][cy]));
             if (D == 2) {
                 fn(cx + 3 * cy, fmaf(drho, pxy, dxy_r));
             } else {
 #pragma unroll
                 for (int cz = 0; cz < 3; ++cz) {
-                    const float psi = pxy * A[2][cz];
-                    const float dpsi_r = fmaf(dxy_r, A[2][cz], p.bxy_r[cx + 3 * cy] * dl[2][cz]);
+                    const float psi = __fmul_rn(pxy, A[2][cz]);
+                    const float dpsi_r = fmaf(dxy_r, A[2][cz], __fmul_rn(p.bxy_r[cx + 3 * cy], dl[2][cz]));
                     fn(cx + 3 * cy + 9 * cz, fmaf(drho, psi, dpsi_r));
                 }
             }
@@ -392,8 +398,8 @@ __device__ __forceinline__ void baseline_args(const StepParams& p, const float* 
 {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        du[a] = u[a] - p.u0[a];
-        dP[a] = fmaf(du[a], u[a] + p.u0[a], corr[a]);
+        du[a] = __fsub_rn(u[a], p.u0[a]);
+        dP[a] = fmaf(du[a], __fadd_rn(u[a], p.u0[a]), corr[a]);
     }
 }
 

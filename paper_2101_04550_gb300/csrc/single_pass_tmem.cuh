@@ -65,7 +65,11 @@ struct TmemLayout {
     static constexpr int off_qx = off_cols + 2 * cols_bytes;         // [kTmaQSlots]
     static constexpr int off_qy = off_qx + kTmaQSlots * qx_bytes;
     static constexpr int off_bar = (off_qy + kTmaQSlots * qy_bytes + 7) / 8 * 8;
-    static constexpr int nbar = 8 + kTmaQSlots;
+    // mbarriers, in this order: full and empty per tile buffer, full and empty
+    // per ring buffer, one per anomaly slot
+    static constexpr int bar_full_t = 0, bar_empty_t = ntile, bar_full_r = 2 * ntile, bar_empty_r = 2 * ntile + 2;
+    static constexpr int bar_qready = 2 * ntile + 4;
+    static constexpr int nbar = bar_qready + kTmaQSlots;
     static constexpr int off_abort = off_bar + 8 * nbar;
     static constexpr int off_tmem = off_abort + 4;
     static constexpr int bytes = off_abort + 16 + 128;               // + slack for aligning the base
@@ -93,11 +97,11 @@ __device__ __forceinline__ void tmem_tile_step(const CUtensorMap* tm_tile, const
     const uint32_t sbase = (raw_addr + 127u) & ~127u;
     unsigned char* base = smem_raw + (sbase - raw_addr);
     const uint32_t bar0 = sbase + L::off_bar;
-    auto full_t = [&](int b) { return bar0 + 8u * b; };
-    auto empty_t = [&](int b) { return bar0 + 8u * (2 + b); };
-    auto full_r = [&](int r) { return bar0 + 8u * (4 + r); };
-    auto empty_r = [&](int r) { return bar0 + 8u * (6 + r); };
-    auto qready = [&](int s) { return bar0 + 8u * (8 + s); };
+    auto full_t = [&](int b) { return bar0 + 8u * (L::bar_full_t + b); };
+    auto empty_t = [&](int b) { return bar0 + 8u * (L::bar_empty_t + b); };
+    auto full_r = [&](int r) { return bar0 + 8u * (L::bar_full_r + r); };
+    auto empty_r = [&](int r) { return bar0 + 8u * (L::bar_empty_r + r); };
+    auto qready = [&](int s) { return bar0 + 8u * (L::bar_qready + s); };
     volatile int* abort_flag = reinterpret_cast<volatile int*>(base + L::off_abort);
 
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1

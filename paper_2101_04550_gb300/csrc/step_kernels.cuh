@@ -89,8 +89,8 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     float u[3], pcorr[3], du[3], dP[3];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        u[a] = j[a] * inv_rho;
-        pcorr[a] = p.coef * inv_rho * d[a];
+        u[a] = __fmul_rn(j[a], inv_rho);
+        pcorr[a] = __fmul_rn(__fmul_rn(p.coef, inv_rho), d[a]);
     }
     baseline_args<D>(p, u, pcorr, du, dP);
     const float om = p.omega;
@@ -122,7 +122,7 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     };
     auto relax_one = [&](int i, float geq) {
         const float gi = gval(i);
-        const float dl = geq - gi;
+        const float dl = __fsub_rn(geq, gi);
         accumulate(i, dl);
         const int k = corrected_slot<D>(i);
         if (k >= 0) {
@@ -135,16 +135,18 @@ __device__ __forceinline__ void relax_streamed(const StepParams& p, G&& gval, P&
     if (POLY) for_each_second_order<D>(p, drho, u, relax_one);
     else for_each_equilibrium<D>(p, drho, du, dP, relax_one);
     auto inc = [&](int k, float v) { return forced ? v + kf[k] : v; };
-    const float hx = 0.5f * ex, hy = 0.5f * ey;
-    put(I0, fmaf(om, inc(0, (keep[0] - gval(I0)) - e0), gval(I0)));
-    put(I0 - 1, fmaf(om, inc(1, (keep[1] - gval(I0 - 1)) + hx), gval(I0 - 1)));
-    put(I0 + 1, fmaf(om, inc(2, (keep[2] - gval(I0 + 1)) - hx), gval(I0 + 1)));
-    put(I0 - 3, fmaf(om, inc(3, (keep[3] - gval(I0 - 3)) + hy), gval(I0 - 3)));
-    put(I0 + 3, fmaf(om, inc(4, (keep[4] - gval(I0 + 3)) - hy), gval(I0 + 3)));
+    const float hx = __fmul_rn(0.5f, ex), hy = __fmul_rn(0.5f, ey);
+    // f*_k - f_k with the half-increment h of its axis: (keep - g) -+ h
+    auto corr = [&](int k, int i, float h) { return inc(k, __fadd_rn(__fsub_rn(keep[k], gval(i)), h)); };
+    put(I0, fmaf(om, inc(0, __fsub_rn(__fsub_rn(keep[0], gval(I0)), e0)), gval(I0)));
+    put(I0 - 1, fmaf(om, corr(1, I0 - 1, hx), gval(I0 - 1)));
+    put(I0 + 1, fmaf(om, corr(2, I0 + 1, -hx), gval(I0 + 1)));
+    put(I0 - 3, fmaf(om, corr(3, I0 - 3, hy), gval(I0 - 3)));
+    put(I0 + 3, fmaf(om, corr(4, I0 + 3, -hy), gval(I0 + 3)));
     if (D == 3) {
-        const float hz = 0.5f * ez;
-        put(I0 - 9, fmaf(om, inc(5, (keep[5] - gval(I0 - 9)) + hz), gval(I0 - 9)));
-        put(I0 + 9, fmaf(om, inc(6, (keep[6] - gval(I0 + 9)) - hz), gval(I0 + 9)));
+        const float hz = __fmul_rn(0.5f, ez);
+        put(I0 - 9, fmaf(om, corr(5, I0 - 9, hz), gval(I0 - 9)));
+        put(I0 + 9, fmaf(om, corr(6, I0 + 9, -hz), gval(I0 + 9)));
     }
 }
 
