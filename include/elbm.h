@@ -171,6 +171,12 @@ int elbm_set_option(elbm_solver* s, int key, double value);
  * Initialise the populations to the product-form equilibrium of the given
  * fields, f_i = rho Psi_i(u, T + u^2, lam) (Eq. 27eq), and reset the step count.
  *   rho  nx*ny*nz values; u  D*nx*ny*nz values; dtype ELBM_DTYPE_F32/F64.
+ *   on_device  nonzero: rho and u are device pointers, read by work enqueued on
+ *        the solver's stream (keep them valid until it has run).  Zero: host
+ *        pointers.  Page-locked host buffers (cudaHostAlloc, cudaHostRegister)
+ *        are read in place by the initialisation kernel, and the call returns
+ *        once they have been read; pageable ones are copied to a device buffer
+ *        first.
  */
 int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_device);
 
@@ -185,7 +191,9 @@ int elbm_step(elbm_solver* s, int n);
 /*
  * Density and velocity of the current (post-streaming) state, Eqs. density and
  * momentum.  With a body force the velocity is the half-step value u + g/2.
- * Synchronises the solver's stream.
+ * Synchronises the solver's stream.  on_device as for elbm_init: page-locked
+ * host buffers are written in place by the moments kernel, pageable ones
+ * through a device buffer.
  */
 int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device);
 

@@ -390,6 +390,20 @@ static cudaError_t stage_to_device(const void* host, size_t bytes, void** dev, c
     return cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st);
 }
 
+// The device address of page-locked host memory mapped into the device's
+// address space (cudaHostAlloc, cudaHostRegister), else nullptr (pageable
+// memory).  Kernels then read or write such a buffer in place: the transfer
+// runs at the link's rate inside the kernel, with no staging copy.
+static void* mapped_host(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_device)
 {
     (void)cudaGetLastError();  // a stale error of an earlier call is not this call's
@@ -400,7 +414,13 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
     const void* du = u;
     void *t1 = nullptr, *t2 = nullptr;
     cudaError_t e = cudaSuccess;
-    if (!on_device) {
+    void* mr = on_device ? nullptr : mapped_host(rho);
+    void* mu = on_device ? nullptr : mapped_host(u);
+    const bool in_place = mr && mu;  // page-locked host fields: read where they are
+    if (in_place) {
+        drho = mr;
+        du = mu;
+    } else if (!on_device) {
         e = stage_to_device(rho, es * s->N, &t1, s->stream);
         if (e == cudaSuccess) e = stage_to_device(u, es * s->D * s->N, &t2, s->stream);
         drho = t1;
@@ -431,6 +451,7 @@ int elbm_init(elbm_solver* s, const void* rho, const void* u, int dtype, int on_
         if (t1) cudaFreeAsync(t1, s->stream);
         if (t2) cudaFreeAsync(t2, s->stream);
     }
+    if (e == cudaSuccess && in_place) e = cudaStreamSynchronize(s->stream);  // the caller's buffers are read
     if (e != cudaSuccess) return cuda_fail(e, "elbm_init");
     s->parity = 0;
     s->steps_done = 0;
@@ -511,18 +532,23 @@ int elbm_moments(elbm_solver* s, void* rho, void* u, int dtype, int on_device)
     const size_t es = dtype == ELBM_DTYPE_F64 ? 8 : 4;
     void *drho = rho, *du = u;
     cudaError_t e = cudaSuccess;
-    if (!on_device) {
+    void* mr = on_device ? nullptr : mapped_host(rho);
+    void* mu = on_device ? nullptr : mapped_host(u);
+    const bool staged = !on_device && !(mr && mu);  // page-locked host fields are written in place
+    if (!on_device && !staged) {
+        drho = mr;
+        du = mu;
+    }
+    if (staged) {
         e = cudaMallocAsync(&drho, es * s->N, s->stream);
         if (e == cudaSuccess) e = cudaMallocAsync(&du, es * s->D * s->N, s->stream);
     }
     if (e == cudaSuccess)
         e = (s->D == 2) ? elbm::moments_impl<2>(*s, drho, du, dtype, &s->launches)
                         : elbm::moments_impl<3>(*s, drho, du, dtype, &s->launches);
-    if (!on_device) {
+    if (staged) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(rho, drho, es * s->N, cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, es * s->D * s->N, cudaMemcpyDeviceToHost, s->stream);
-    }
-    if (!on_device) {
         cudaFreeAsync(drho, s->stream);
         cudaFreeAsync(du, s->stream);
     }
