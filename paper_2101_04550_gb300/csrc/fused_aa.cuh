@@ -5,16 +5,21 @@
 // anomaly Q~ (Eq. Deviation) of the whole grid, once more to collide --
 // because the central difference of Eq. Paastar1 needs the anomaly of the face
 // neighbours at the same time level.  Here a block owns a 32 x 8 tile column
-// and marches along z with the anomaly kFuLookahead (L) planes ahead of the
-// collision:
-//   iteration z:  gather plane z+L (AA read slots), moments, anomaly; write
-//                 Q~_xxx, Q~_yyy of plane z+L to the anomaly field (Q~_zzz
-//                 goes to a ring of registers); publish "planes 0..z+L
-//                 done"; wait until the four face-neighbouring tile columns
-//                 have published plane z (done L iterations earlier, so the
-//                 wait rarely blocks); gather plane z again -- read L planes
-//                 ago, so mostly from L2 -- and collide it (Eqs. Paastar1,
-//                 27eqext, LBGK), scattering to the AA write slots.
+// and marches along z with the anomaly one plane ahead of the collision; each
+// thread copies its node's populations (its AA read slots) into a column of a
+// shared-memory stage with cp.async two planes before it collides them, and
+// reads them from there for both the anomaly and the collision:
+//   iteration z:  start the copy of plane z+2 (into the stage of plane z-1,
+//                 collided last iteration); wait for the copy of plane z+1;
+//                 its moments and anomaly: write Q~_xxx, Q~_yyy of plane z+1
+//                 to the anomaly field (Q~_zzz goes to a ring of registers);
+//                 publish "planes 0..z+1 done"; wait until the four
+//                 face-neighbouring tile columns have published plane z
+//                 (done an iteration earlier, so the wait rarely blocks);
+//                 collide plane z from its stage (Eqs. Paastar1, 27eqext,
+//                 LBGK), scattering to the AA write slots.
+// A population is read from DRAM once, and the copy of a plane runs while the
+// block collides the plane before it.
 // The z difference of plane 0 needs Q~_zzz of plane nz-1, which a prologue
 // computes first (from the same, still untouched slots); the z difference of
 // plane nz-1 needs Q~_zzz of plane 0, kept from before plane 0 was collided
@@ -31,7 +36,9 @@
 // launch); every wait is bounded in time and, when it gives up, sets
 // ELBM_ERR_TIMEOUT in the status word and stops the block.
 //
-// The per-node arithmetic is the two-pass form's (gather, moments, anomaly,
+// Staged copies cannot go stale: the slots a node reads in a step are the
+// ones it writes, and only its own collision writes them.  The per-node
+// arithmetic is the two-pass form's (staged gather, moments, anomaly,
 // relax_streamed, scatter through the AA slots), so the results agree bit for
 // bit.
 #pragma once
@@ -69,14 +76,23 @@ __device__ __forceinline__ bool bounded_progress_wait(const unsigned long long* 
     return true;
 }
 
-// Planes the anomaly runs ahead of the collision.
-constexpr int kFuLookahead = 2;
+// Planes the anomaly runs ahead of the collision, and the shared-memory
+// stage: a column of 27 words per thread for each plane between its anomaly
+// and its collision, plus the one being fetched.
+constexpr int kFuLookahead = 1;
+constexpr int kFuBufs = kFuLookahead + 2;
+constexpr int kFuStageWords = kFuBufs * 27 * kFuThreads;
+constexpr int kFuSmemBytes = (kFuStageWords + kFuBufs * kFuThreads) * 4;
 
 template <int ST, int PAR>
-__global__ void __launch_bounds__(kFuThreads, 3)
+__global__ void __launch_bounds__(kFuThreads, 2)
     k_fused_aa(const __grid_constant__ StepParams p, unsigned long long* progress, unsigned long long epoch)
 {
-    constexpr int D = 3, LA = kFuLookahead;
+    static_assert(kFuLookahead == 1, "the cp.async group count below assumes one plane of look-ahead");
+    constexpr int D = 3;
+    extern __shared__ __align__(16) unsigned fu_smem[];
+    unsigned* stage = fu_smem;                  // [kFuBufs][27][kFuThreads]
+    unsigned* hmask = fu_smem + kFuStageWords;  // [kFuBufs][kFuThreads]: bit i, population i in the upper half
     const int tx = threadIdx.x % kFuTileX, ty = threadIdx.x / kFuTileX;
     const int gx = blockIdx.x * kFuTileX + tx, gy = blockIdx.y * kFuTileY + ty;
     const bool active = gx < p.nx && gy < p.ny;
@@ -94,37 +110,66 @@ __global__ void __launch_bounds__(kFuThreads, 3)
     float* qy = p.q + p.N;
     // node (gx, gy, z); inactive threads of a ragged tile take a valid node and do nothing with it
     auto node_at = [&](int z) { return make_node<D>(p, (active ? gx + gy * p.nx : 0) + z * p.plane); };
-    // anomaly of the node at plane z: Q~_xxx, Q~_yyy to the field, Q~_zzz returned
-    auto anomaly_plane = [&](int z, bool publish_xy) {
+    // copy the own node's populations at plane z (its AA read slots) into its stage column
+    auto stage_plane = [&](int z) {
         const Node n = node_at(z);
+        unsigned* c = stage + (z % kFuBufs) * 27 * kFuThreads + threadIdx.x;
+        unsigned h = 0;
+#pragma unroll
+        for (int i = 0; i < 27; ++i) {
+            const int idx = read_slot<D>(n, p.N, i, PAR);
+            h |= (unsigned)(idx & 1) << i;
+            cp_async4(c + i * kFuThreads, stage_src<ST>(p, idx));
+        }
+        hmask[(z % kFuBufs) * kFuThreads + threadIdx.x] = h;
+    };
+    // population i of the own node at plane z, from the stage
+    auto staged = [&](int z) {
+        const unsigned* c = stage + (z % kFuBufs) * 27 * kFuThreads + threadIdx.x;
+        const unsigned h = hmask[(z % kFuBufs) * kFuThreads + threadIdx.x];
+        return [=, &p](int i) { return stage_value<ST>(p, ld_stage(c + i * kFuThreads), (int)((h >> i) & 1u), i); };
+    };
+    // anomaly of the own node at plane z from the stage: Q~_xxx, Q~_yyy to the field, Q~_zzz returned
+    auto anomaly_staged = [&](int z) {
+        float drho, j[3];
+        moments_of<D>(p, staged(z), drho, j);
+        const float inv = 1.0f / (p.rho_ref + drho);
+        const int cell = gx + gy * p.nx + z * p.plane;
+        qx[cell] = anomaly(p, 0, j[0], j[0] * inv);
+        qy[cell] = anomaly(p, 1, j[1], j[1] * inv);
+        return anomaly(p, 2, j[2], j[2] * inv);
+    };
+    // ring[k]: Q~_zzz of the own node at plane z - 1 + k, k = 0 .. 2
+    float ring[3] = {0.f, 0.f, 0.f};
+    float qz_first = 0.f;
+    if (active) {
+        // plane -1 (periodic: nz-1), straight from its slots, which no collision has touched yet
+        const Node n = node_at(p.nz - 1);
         float g[27], drho, j[3];
         gather<D, ST, PAR>(p, n, g);
         moments<D>(p, g, drho, j);
         const float inv = 1.0f / (p.rho_ref + drho);
-        if (publish_xy) {
-            qx[n.cell] = anomaly(p, 0, j[0], j[0] * inv);
-            qy[n.cell] = anomaly(p, 1, j[1], j[1] * inv);
-        }
-        return anomaly(p, 2, j[2], j[2] * inv);
-    };
-    // ring[k]: Q~_zzz of the own node at plane z - 1 + k, k = 0 .. LA + 1
-    float ring[LA + 2];
-#pragma unroll
-    for (int k = 0; k < LA + 2; ++k) ring[k] = 0.f;
-    float qz_first = 0.f;
-    if (active) {
-        ring[0] = anomaly_plane(p.nz - 1, false);  // plane -1, periodic
-#pragma unroll
-        for (int k = 0; k < LA; ++k)
-            if (k < p.nz) ring[k + 1] = anomaly_plane(k, true);
-        qz_first = ring[1];  // plane 0, before it is collided
+        ring[0] = anomaly(p, 2, j[2], j[2] * inv);
     }
+    // planes 0 and 1 into the stage (always two cp.async groups, so that the
+    // "all but the newest group" waits below name the right plane)
+    stage_plane(0);
+    cp_async_commit();
+    if (p.nz > 1) stage_plane(1);
+    cp_async_commit();
+    cp_async_wait_prior();  // plane 0 is in
+    if (active) ring[1] = anomaly_staged(0);
+    qz_first = ring[1];  // plane 0, before it is collided
     for (int z = 0; z < p.nz; ++z) {
-        // ------------------------------------------ anomaly of plane z + LA
-        const int za = z + LA;
+        const int za = z + 1;
+        // --------------- fetch plane z + 2 into the stage of plane z - 1 (collided)
+        if (za + 1 < p.nz) stage_plane(za + 1);
+        cp_async_commit();
+        cp_async_wait_prior();  // plane z + 1 is in
+        // ------------------------------------------ anomaly of plane z + 1
         float qa = za == p.nz ? qz_first : 0.f;
-        if (active && za < p.nz) qa = anomaly_plane(za, true);
-        ring[LA + 1] = qa;
+        if (active && za < p.nz) qa = anomaly_staged(za);
+        ring[2] = qa;
         // --------------------------------- publish, wait for the neighbours
         // (the release store after the block barrier orders every thread's
         // anomaly writes before the counter; lanes 0..3 of warp 0 then wait
@@ -137,13 +182,13 @@ __global__ void __launch_bounds__(kFuThreads, 3)
                 s_abort = 1;
         }
         __syncthreads();
-        if (s_abort) return;
-        // ---------------------------- collide plane z (gathered once more)
+        if (s_abort) break;
+        // ------------------------- collide plane z (from its stage column)
         if (active) {
             const Node n = node_at(z);
-            float g[27], drho, j[3];
-            gather<D, ST, PAR>(p, n, g);
-            moments<D>(p, g, drho, j);
+            auto gv = staged(z);
+            float drho, j[3];
+            moments_of<D>(p, gv, drho, j);
             float d[3] = {0.f, 0.f, 0.f};
             if (p.eq_mode == 0) {
                 d[0] = (__ldcg(qx + n.at(1, 0, 0)) - __ldcg(qx + n.at(-1, 0, 0))) * p.inv_2lam[0];
@@ -157,11 +202,12 @@ __global__ void __launch_bounds__(kFuThreads, 3)
                 const int slot = (PAR == 0) ? (26 - i) * p.N + cell_o : write_slot<D>(n, p.N, i, PAR);
                 S::store(f + slot, S::shifted ? v : fmaf(p.bw[i], p.rho_ref, v));
             };
-            relax_streamed<D>(p, [&](int i) { return g[i]; }, put, drho, j, d);
+            relax_streamed<D>(p, gv, put, drho, j, d);
         }
-#pragma unroll
-        for (int k = 0; k < LA + 1; ++k) ring[k] = ring[k + 1];
+        ring[0] = ring[1];
+        ring[1] = ring[2];
     }
+    cp_async_wait_all();  // no copy may still be in flight when the block retires
 }
 
 // Whether the fused form takes solver s and how many of its blocks fit the GPU at once.
@@ -171,7 +217,10 @@ bool fused_fits(const Solver& s, int* blocks_x, int* blocks_y)
     *blocks_x = (s.nx + kFuTileX - 1) / kFuTileX;
     *blocks_y = (s.ny + kFuTileY - 1) / kFuTileY;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_aa<ST, 0>, kFuThreads, 0) != cudaSuccess) {
+    if (set_smem_limit_once<k_fused_aa<ST, 0>>(kFuSmemBytes) != cudaSuccess ||
+        set_smem_limit_once<k_fused_aa<ST, 1>>(kFuSmemBytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_aa<ST, 0>, kFuThreads, kFuSmemBytes) !=
+            cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
