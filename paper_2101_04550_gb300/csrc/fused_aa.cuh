@@ -19,7 +19,12 @@
 //                 collide plane z from its stage (Eqs. Paastar1, 27eqext,
 //                 LBGK), scattering to the AA write slots.
 // A population is read from DRAM once, and the copy of a plane runs while the
-// block collides the plane before it.
+// block collides the plane before it.  Publishing and waiting belong to a
+// ninth warp: the consumers signal "anomaly of plane z+1 written" and wait
+// for "neighbours have plane z" through shared-memory mbarriers and never
+// stop at a block-wide barrier; the progress warp releases the block's
+// counter once they have written, and acquires the neighbours' counters
+// before it lets them collide.
 // The z difference of plane 0 needs Q~_zzz of plane nz-1, which a prologue
 // computes first (from the same, still untouched slots); the z difference of
 // plane nz-1 needs Q~_zzz of plane 0, kept from before plane 0 was collided
@@ -77,15 +82,18 @@ __device__ __forceinline__ bool bounded_progress_wait(const unsigned long long* 
 }
 
 // Planes the anomaly runs ahead of the collision, and the shared-memory
-// stage: a column of 27 words per thread for each plane between its anomaly
-// and its collision, plus the one being fetched.
+// stage: a column of 27 words per consumer thread for each plane between its
+// anomaly and its collision, plus the one being fetched.
 constexpr int kFuLookahead = 1;
 constexpr int kFuBufs = kFuLookahead + 2;
 constexpr int kFuStageWords = kFuBufs * 27 * kFuThreads;
 constexpr int kFuSmemBytes = (kFuStageWords + kFuBufs * kFuThreads) * 4;
+// block: the consumer threads (one node each) + one warp that publishes the
+// block's progress and acquires the neighbours'
+constexpr int kFuBlock = kFuThreads + 32;
 
 template <int ST, int PAR>
-__global__ void __launch_bounds__(kFuThreads, 2)
+__global__ void __launch_bounds__(kFuBlock, 2)
     k_fused_aa(const __grid_constant__ StepParams p, unsigned long long* progress, unsigned long long epoch)
 {
     static_assert(kFuLookahead == 1, "the cp.async group count below assumes one plane of look-ahead");
@@ -93,19 +101,66 @@ __global__ void __launch_bounds__(kFuThreads, 2)
     extern __shared__ __align__(16) unsigned fu_smem[];
     unsigned* stage = fu_smem;                  // [kFuBufs][27][kFuThreads]
     unsigned* hmask = fu_smem + kFuStageWords;  // [kFuBufs][kFuThreads]: bit i, population i in the upper half
-    const int tx = threadIdx.x % kFuTileX, ty = threadIdx.x / kFuTileX;
-    const int gx = blockIdx.x * kFuTileX + tx, gy = blockIdx.y * kFuTileY + ty;
-    const bool active = gx < p.nx && gy < p.ny;
+    // published(k & 1): the consumers wrote the anomaly of planes 0..k (count
+    // kFuThreads); ready(z & 1): the four neighbouring tile columns have
+    // released plane z (count 1).  Two of each suffice: the consumers arrive
+    // on published(k+2) only after passing ready(k), which the progress warp
+    // signals after observing published(k); it signals ready(z+2) only after
+    // observing published(z+2), which the consumers arrive on after passing
+    // ready(z).
+    __shared__ __align__(8) unsigned long long s_bar[4];
+    __shared__ int s_abort;
+    const uint32_t bar0 = smem_u32(s_bar);
+    auto published = [&](int k) { return bar0 + 8u * (k & 1); };
+    auto ready = [&](int z) { return bar0 + 8u * (2 + (z & 1)); };
+    volatile int* abort_flag = &s_abort;
+    if (threadIdx.x == 0) {
+        mbar_init(published(0), kFuThreads);
+        mbar_init(published(1), kFuThreads);
+        mbar_init(ready(0), 1);
+        mbar_init(ready(1), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     const int bx = blockIdx.x, by = blockIdx.y, nbx = gridDim.x, nby = gridDim.y;
     const unsigned long long base = epoch * (unsigned long long)(p.nz + 2);
-    // the four face-neighbouring tile columns (periodic)
-    const int nb[4] = {by * nbx + (bx == 0 ? nbx - 1 : bx - 1), by * nbx + (bx == nbx - 1 ? 0 : bx + 1),
-                       (by == 0 ? nby - 1 : by - 1) * nbx + bx, (by == nby - 1 ? 0 : by + 1) * nbx + bx};
-    const int me = by * nbx + bx;
-    __shared__ int s_abort;
-    if (threadIdx.x == 0) s_abort = 0;
-    __syncthreads();
 
+    if (threadIdx.x >= kFuThreads) {
+        // ------------------------------------------------ progress warp
+        // publication k = "planes 0..k of the anomaly written" is released
+        // as counter value base + k + 1, after the consumers' arrivals on
+        // published(k); ready(z) is signalled once all four neighbours have
+        // released plane z.  Acquiring plane z comes before waiting for the
+        // block's own publication z + 1, so that the consumers, who publish
+        // z + 1 before they need plane z, never wait on their own release.
+        const int lane = threadIdx.x & 31;
+        const int me = by * nbx + bx;
+        const int nb[4] = {by * nbx + (bx == 0 ? nbx - 1 : bx - 1), by * nbx + (bx == nbx - 1 ? 0 : bx + 1),
+                           (by == 0 ? nby - 1 : by - 1) * nbx + bx, (by == nby - 1 ? 0 : by + 1) * nbx + bx};
+        auto release = [&](int k) {
+            if (!bounded_wait(published(k), (unsigned)(k >> 1) & 1u, abort_flag, p.status, kTmaWaitNs)) return false;
+            if (lane == 0) st_release_u64(progress + me, base + (unsigned long long)(k + 1));
+            return true;
+        };
+        if (!__all_sync(0xffffffffu, release(0))) return;
+        for (int z = 0; z < p.nz; ++z) {
+            bool ok = true;
+            if (lane < 4) {
+                ok = bounded_progress_wait(progress + nb[lane], base + (unsigned long long)(z + 1), p.status,
+                                           globaltimer_ns(), kTmaWaitNs);
+                if (!ok) *abort_flag = 1;
+            }
+            if (!__all_sync(0xffffffffu, ok)) return;
+            if (lane == 0) mbar_arrive(ready(z));
+            if (z + 1 < p.nz && !__all_sync(0xffffffffu, release(z + 1))) return;
+        }
+        return;
+    }
+    // ------------------------------------------------------ consumers
+    const int tx = threadIdx.x % kFuTileX, ty = threadIdx.x / kFuTileX;
+    const int gx = bx * kFuTileX + tx, gy = by * kFuTileY + ty;
+    const bool active = gx < p.nx && gy < p.ny;
     float* qx = p.q;
     float* qy = p.q + p.N;
     // node (gx, gy, z); inactive threads of a ragged tile take a valid node and do nothing with it
@@ -141,7 +196,6 @@ __global__ void __launch_bounds__(kFuThreads, 2)
     };
     // ring[k]: Q~_zzz of the own node at plane z - 1 + k, k = 0 .. 2
     float ring[3] = {0.f, 0.f, 0.f};
-    float qz_first = 0.f;
     if (active) {
         // plane -1 (periodic: nz-1), straight from its slots, which no collision has touched yet
         const Node n = node_at(p.nz - 1);
@@ -159,30 +213,23 @@ __global__ void __launch_bounds__(kFuThreads, 2)
     cp_async_commit();
     cp_async_wait_prior();  // plane 0 is in
     if (active) ring[1] = anomaly_staged(0);
-    qz_first = ring[1];  // plane 0, before it is collided
+    mbar_arrive(published(0));
+    const float qz_first = ring[1];  // plane 0, before it is collided
     for (int z = 0; z < p.nz; ++z) {
         const int za = z + 1;
         // --------------- fetch plane z + 2 into the stage of plane z - 1 (collided)
         if (za + 1 < p.nz) stage_plane(za + 1);
         cp_async_commit();
         cp_async_wait_prior();  // plane z + 1 is in
-        // ------------------------------------------ anomaly of plane z + 1
-        float qa = za == p.nz ? qz_first : 0.f;
-        if (active && za < p.nz) qa = anomaly_staged(za);
-        ring[2] = qa;
-        // --------------------------------- publish, wait for the neighbours
-        // (the release store after the block barrier orders every thread's
-        // anomaly writes before the counter; lanes 0..3 of warp 0 then wait
-        // on the four neighbours side by side)
-        __syncthreads();
-        if (threadIdx.x == 0) st_release_u64(progress + me, base + (unsigned long long)min(za + 1, p.nz));
-        if (threadIdx.x < 4) {
-            const unsigned long long need = base + (unsigned long long)(z + 1);
-            if (!bounded_progress_wait(progress + nb[threadIdx.x], need, p.status, globaltimer_ns(), kTmaWaitNs))
-                s_abort = 1;
+        // ----------------------------- anomaly of plane z + 1, published
+        float qa = qz_first;
+        if (za < p.nz) {
+            if (active) qa = anomaly_staged(za);
+            mbar_arrive(published(za));
         }
-        __syncthreads();
-        if (s_abort) break;
+        ring[2] = qa;
+        // --------------- wait until the neighbouring columns have plane z
+        if (!bounded_wait(ready(z), (unsigned)(z >> 1) & 1u, abort_flag, p.status, kTmaWaitNs)) break;
         // ------------------------- collide plane z (from its stage column)
         if (active) {
             const Node n = node_at(z);
@@ -219,7 +266,7 @@ bool fused_fits(const Solver& s, int* blocks_x, int* blocks_y)
     int per_sm = 0;
     if (set_smem_limit_once<k_fused_aa<ST, 0>>(kFuSmemBytes) != cudaSuccess ||
         set_smem_limit_once<k_fused_aa<ST, 1>>(kFuSmemBytes) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_aa<ST, 0>, kFuThreads, kFuSmemBytes) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_aa<ST, 0>, kFuBlock, kFuSmemBytes) !=
             cudaSuccess) {
         (void)cudaGetLastError();
         return false;

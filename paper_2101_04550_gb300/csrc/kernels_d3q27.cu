@@ -47,7 +47,7 @@ cudaError_t step_fused_impl(const Solver& s, int parity, unsigned long long* pro
     cudaError_t e = cudaSuccess;
     ELBM_DISPATCH_STORAGE(s.storage, {
         const void* fn = parity == 0 ? (const void*)k_fused_aa<ST, 0> : (const void*)k_fused_aa<ST, 1>;
-        e = cudaLaunchCooperativeKernel(fn, grid, dim3(kFuThreads), args, kFuSmemBytes, s.stream);
+        e = cudaLaunchCooperativeKernel(fn, grid, dim3(kFuBlock), args, kFuSmemBytes, s.stream);
     });
     if (e == cudaSuccess) ++*launches;
     return e;
